@@ -1,0 +1,60 @@
+/*
+ * kmc_oracle.h -- interface of the plain FP64 CPU oracle (test infrastructure
+ * only; see kmc_oracle.c for the readings of the paper it implements).
+ * This header belongs to the oracle alone; the CUDA path does not include it.
+ */
+#ifndef KMC_ORACLE_H
+#define KMC_ORACLE_H
+
+#include <stdint.h>
+
+#define ORC_MAX_ZONES 32
+/* step index of the initial-placement stream (never a simulated step) */
+#define ORC_INIT_STEP 0xFFFFFFFFu
+
+typedef struct {
+    int32_t R;          /* rails */
+    int32_t L;          /* sites per rail */
+    int32_t Z;          /* zones (S2.1.5) */
+    int32_t electrodes; /* 0 blocking, 1 injecting/extracting */
+    double d;           /* hop distance d_hop (nm) */
+    double dt;          /* time step (s) */
+    double T;           /* temperature (K) */
+    double Ea;          /* migration barrier (eV), Eq. 1 */
+    double nu;          /* attempt frequency (Hz), Eq. 1 */
+    double alpha;       /* volts per excess ion of the rail-local space charge */
+    double kappa;       /* dimensionless coupling of the space-charge term */
+    double k_e;         /* electrode exchange rate (Hz) */
+    double rho_e;       /* reservoir density in [0, 1] */
+    uint64_t seed;      /* Philox key */
+    uint32_t instance;  /* fourth Philox counter word */
+    int32_t pad;
+} orc_params;
+
+typedef struct {
+    int32_t rail;
+    uint32_t step;
+    int32_t site;
+    int32_t dir;  /* 0 right trial, 1 left trial */
+    int32_t kind; /* 0 inner hop, 1 injection, 2 extraction */
+    int32_t pad;
+    double diff;  /* u - p */
+} orc_log_entry;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+int orc_zone_of(int k, int L, int Z);
+void orc_zone_widths(int L, int Z, int32_t *w);
+double orc_gamma0(double nu, double Ea, double T);
+double orc_p0(double nu, double Ea, double T, double dt);
+void orc_p0_table(const orc_params *P, const double *Ea_site, double *P0);
+void orc_hop_probs(double base, double B, double inv, double *p_left, double *p_right);
+void orc_zone_field(const orc_params *P, const int32_t *Nz, int32_t N0, double V, double *dV,
+                    double *B, double *inv);
+int orc_init_occupancy(const orc_params *P, int mode, int64_t n_ions, double fill, uint8_t *occ);
+int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, uint8_t *occ,
+            const int32_t *N0, const double *P0site, int64_t *J_out, int64_t *Zc_out,
+            int64_t *J_rail, orc_log_entry *log, int64_t log_cap, int64_t *log_count,
+            int nthreads);
+int orc_max_threads(void);
+
+#endif

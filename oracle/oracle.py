@@ -1,0 +1,237 @@
+"""ctypes front end of the FP64 C oracle (kmc_oracle.c).
+
+Test infrastructure only: it builds and loads ``liboracle.so`` from the C
+source next to it.  Every function here is a thin marshalling wrapper; the
+arithmetic of the method is in kmc_oracle.c.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kmc_oracle.c")
+_HDR = os.path.join(_HERE, "kmc_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+INIT_STEP = 0xFFFFFFFF
+MAX_ZONES = 32
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("R", ctypes.c_int32), ("L", ctypes.c_int32), ("Z", ctypes.c_int32),
+        ("electrodes", ctypes.c_int32),
+        ("d", ctypes.c_double), ("dt", ctypes.c_double), ("T", ctypes.c_double),
+        ("Ea", ctypes.c_double), ("nu", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("k_e", ctypes.c_double), ("rho_e", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32), ("pad", ctypes.c_int32),
+    ]
+
+
+class OrcLogEntry(ctypes.Structure):
+    _fields_ = [
+        ("rail", ctypes.c_int32), ("step", ctypes.c_uint32), ("site", ctypes.c_int32),
+        ("dir", ctypes.c_int32), ("kind", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("diff", ctypes.c_double),
+    ]
+
+
+LOG_DTYPE = np.dtype([("rail", "<i4"), ("step", "<u4"), ("site", "<i4"), ("dir", "<i4"),
+                      ("kind", "<i4"), ("pad", "<i4"), ("diff", "<f8")])
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (gcc, FP64, no contraction, OpenMP over rails)."""
+    with _lock:
+        fresh = (os.path.exists(_LIB)
+                 and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+        if force or not fresh:
+            tmp = _LIB + ".tmp%d" % os.getpid()
+            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                   "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True, cwd=_HERE)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        P = ctypes.POINTER(OrcParams)
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_zone_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_zone_of.restype = ctypes.c_int
+        L.orc_zone_widths.argtypes = [ctypes.c_int, ctypes.c_int, i32p]
+        L.orc_gamma0.argtypes = [ctypes.c_double] * 3
+        L.orc_gamma0.restype = ctypes.c_double
+        L.orc_p0.argtypes = [ctypes.c_double] * 4
+        L.orc_p0.restype = ctypes.c_double
+        L.orc_p0_table.argtypes = [P, f64p, f64p]
+        L.orc_hop_probs.argtypes = [ctypes.c_double] * 3 + [f64p, f64p]
+        L.orc_zone_field.argtypes = [P, i32p, ctypes.c_int32, ctypes.c_double, f64p, f64p, f64p]
+        L.orc_init_occupancy.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_double, u8p]
+        L.orc_init_occupancy.restype = ctypes.c_int
+        L.orc_run.argtypes = [P, f64p, ctypes.c_int64, ctypes.c_int64, u8p, i32p, f64p, i64p,
+                              i64p, i64p, ctypes.POINTER(OrcLogEntry), ctypes.c_int64, i64p,
+                              ctypes.c_int]
+        L.orc_run.restype = ctypes.c_int
+        L.orc_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray], ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def params(dev) -> OrcParams:
+    """Oracle parameter block from a workloads.Device (or a dict)."""
+    d = dev if isinstance(dev, dict) else dev.as_dict()
+    return OrcParams(R=d["R"], L=d["L"], Z=d["Z"], electrodes=d["electrodes"], d=d["d"],
+                     dt=d["dt"], T=d["T"], Ea=d["Ea"], nu=d["nu"], alpha=d["alpha"],
+                     kappa=d["kappa"], k_e=d["k_e"], rho_e=d["rho_e"],
+                     seed=d["seed"] & 0xFFFFFFFFFFFFFFFF, instance=d["instance"], pad=0)
+
+
+# ------------------------------------------------------------- primitives
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                            _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def zone_of(k: int, L: int, Z: int) -> int:
+    return lib().orc_zone_of(k, L, Z)
+
+
+def zone_widths(L: int, Z: int) -> np.ndarray:
+    w = np.zeros(Z, dtype=np.int32)
+    lib().orc_zone_widths(L, Z, _ptr(w, ctypes.c_int32))
+    return w
+
+
+def gamma0(nu: float, Ea: float, T: float) -> float:
+    return lib().orc_gamma0(nu, Ea, T)
+
+
+def p0(nu: float, Ea: float, T: float, dt: float) -> float:
+    return lib().orc_p0(nu, Ea, T, dt)
+
+
+def p0_table(dev, Ea_site: np.ndarray) -> np.ndarray:
+    P = params(dev)
+    Ea = np.ascontiguousarray(Ea_site, dtype=np.float64)
+    out = np.empty(Ea.shape, dtype=np.float64)
+    lib().orc_p0_table(ctypes.byref(P), _ptr(Ea, ctypes.c_double), _ptr(out, ctypes.c_double))
+    return out
+
+
+def hop_probs(base: float, B: float, inv: float):
+    """(p_left, p_right) of Eqs. 5-6 for a base probability and a zone's B."""
+    pl = ctypes.c_double()
+    pr = ctypes.c_double()
+    lib().orc_hop_probs(float(base), float(B), float(inv), ctypes.byref(pl), ctypes.byref(pr))
+    return pl.value, pr.value
+
+
+def zone_field(dev, Nz, N0: int, V: float):
+    """(dV, B, inv) per zone for zone counts Nz of one rail."""
+    P = params(dev)
+    n = np.ascontiguousarray(Nz, dtype=np.int32)
+    Z = P.Z
+    dV = np.empty(Z)
+    B = np.empty(Z)
+    inv = np.empty(Z)
+    lib().orc_zone_field(ctypes.byref(P), _ptr(n, ctypes.c_int32), int(N0), float(V),
+                         _ptr(dV, ctypes.c_double), _ptr(B, ctypes.c_double),
+                         _ptr(inv, ctypes.c_double))
+    return dV, B, inv
+
+
+def init_occupancy(dev, mode: int, n_ions: int = 0, fill: float = 0.0) -> np.ndarray:
+    P = params(dev)
+    occ = np.zeros((P.R, P.L), dtype=np.uint8)
+    rc = lib().orc_init_occupancy(ctypes.byref(P), int(mode), int(n_ions), float(fill),
+                                  _ptr(occ, ctypes.c_uint8))
+    if rc != 0:
+        raise ValueError("orc_init_occupancy failed (%d)" % rc)
+    return occ
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
+
+
+# ------------------------------------------------------------- simulation
+
+class OracleSim:
+    """Oracle state of one device: occupancy, N0 per rail, step counter."""
+
+    def __init__(self, dev, V: np.ndarray, occ0: np.ndarray, Ea_site: Optional[np.ndarray] = None,
+                 log_cap: int = 4096, nthreads: int = 0):
+        self.dev = dev
+        self.P = params(dev)
+        self.V = np.ascontiguousarray(V, dtype=np.float64)
+        self.occ = np.ascontiguousarray(occ0, dtype=np.uint8).reshape(self.P.R, self.P.L).copy()
+        self.N0 = self.occ.sum(axis=1).astype(np.int32)
+        self.P0site = p0_table(dev, Ea_site) if Ea_site is not None else None
+        self.t = 0
+        self.J_rail = np.zeros(self.P.R, dtype=np.int64)
+        self.log = np.zeros(log_cap, dtype=LOG_DTYPE)
+        self.log_count = np.zeros(1, dtype=np.int64)
+        self.nthreads = nthreads
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        dev = wl.device
+        if wl.init_mode == 2:
+            occ0 = wl.occ0
+        else:
+            occ0 = init_occupancy(dev, wl.init_mode, wl.n_ions, wl.fill)
+        return cls(dev, wl.V, occ0, wl.Ea_site, **kw)
+
+    def step_n(self, n: int):
+        """Advance n steps; returns (J[n], Zc[n, Z]) for those steps."""
+        P = self.P
+        J = np.zeros(n, dtype=np.int64)
+        Zc = np.zeros((n, P.Z), dtype=np.int64)
+        rc = lib().orc_run(ctypes.byref(P), _ptr(self.V, ctypes.c_double), self.t, n,
+                           _ptr(self.occ, ctypes.c_uint8), _ptr(self.N0, ctypes.c_int32),
+                           _ptr(self.P0site, ctypes.c_double), _ptr(J, ctypes.c_int64),
+                           _ptr(Zc, ctypes.c_int64), _ptr(self.J_rail, ctypes.c_int64),
+                           self.log.ctypes.data_as(ctypes.POINTER(OrcLogEntry)),
+                           len(self.log), _ptr(self.log_count, ctypes.c_int64), self.nthreads)
+        if rc != 0:
+            raise ValueError("orc_run failed (%d)" % rc)
+        self.t += n
+        return J, Zc
+
+    def near_threshold_log(self) -> np.ndarray:
+        n = int(min(self.log_count[0], len(self.log)))
+        return self.log[:n].copy()
+
+
+__all__ = ["build", "lib", "philox4x32_10", "zone_of", "zone_widths", "gamma0", "p0",
+           "p0_table", "zone_field", "hop_probs", "init_occupancy", "max_threads", "OracleSim", "params",
+           "INIT_STEP", "MAX_ZONES", "LOG_DTYPE"]

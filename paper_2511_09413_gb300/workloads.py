@@ -1,0 +1,135 @@
+"""Seeded synthetic workloads for the rail-based KMC sweep.
+
+This module is the one piece shared by the CUDA path, the oracle, the tests
+and the benchmark.  It holds device descriptions (sizes and physical
+parameters), the applied-voltage protocols as per-step tables, and seeded
+random inputs (initial occupancies, per-site barriers).  It holds none of the
+method's arithmetic: no field, rate, probability or update rule.
+
+Protocols follow the paper's simulation types (Supplementary S2.2.2-S2.2.4,
+Table S1): relaxation decay (polarise, then hold a constant voltage) and the
+hysteresis sweep.  The hysteresis waveform is the triangle
+0 -> +A -> 0 -> -A -> 0 per cycle, sampled at the start of each step.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Device:
+    """Physical description of one simulated device (one instance).
+
+    Units: lengths in nm, energies in eV, times in s, rates in Hz, volts.
+    ``alpha`` is the rail-local space-charge voltage per excess ion and
+    ``kappa`` its dimensionless coupling; ``electrodes`` is 0 for blocking and
+    1 for injecting/extracting contacts with exchange rate ``k_e`` and
+    reservoir density ``rho_e``.
+    """
+
+    R: int
+    L: int
+    Z: int = 10
+    electrodes: int = 0
+    d: float = 1.0
+    dt: float = 1e-9
+    T: float = 300.0
+    Ea: float = 0.40
+    nu: float = 1e12
+    alpha: float = 0.2
+    kappa: float = 1.0
+    k_e: float = 0.0
+    rho_e: float = 0.0
+    seed: int = 0
+    instance: int = 0
+
+    def as_dict(self) -> dict:
+        return dataclasses.asdict(self)
+
+
+@dataclasses.dataclass
+class Workload:
+    """A device, its voltage table, its initial condition and its barriers."""
+
+    name: str
+    device: Device
+    V: np.ndarray                      # float64 [n_steps]
+    init_mode: int                     # 0 exact count, 1 Bernoulli(fill), 2 given occupancy
+    n_ions: int = 0
+    fill: float = 0.0
+    occ0: Optional[np.ndarray] = None  # uint8 [R, L] when init_mode == 2
+    Ea_site: Optional[np.ndarray] = None  # float64 [R, L] or None (scalar Ea)
+
+    @property
+    def n_steps(self) -> int:
+        return int(self.V.shape[0])
+
+
+# ---------------------------------------------------------------- protocols
+
+def relaxation_protocol(n_polarise: int, V_polarise: float, n_total: int,
+                        V_hold: float = 0.0) -> np.ndarray:
+    """Relaxation decay (S2.2.2): V_polarise for n_polarise steps, then V_hold."""
+    V = np.full(n_total, float(V_hold), dtype=np.float64)
+    V[:n_polarise] = float(V_polarise)
+    return V
+
+
+def triangle_protocol(amplitude: float, steps_per_cycle: int, cycles: int) -> np.ndarray:
+    """Hysteresis sweep (S2.2.3): 0 -> +A -> 0 -> -A -> 0 per cycle."""
+    t = np.arange(steps_per_cycle * cycles, dtype=np.float64)
+    phase = np.mod(t, steps_per_cycle) / float(steps_per_cycle)
+    tri = np.where(phase < 0.25, 4.0 * phase,
+                   np.where(phase < 0.75, 2.0 - 4.0 * phase, 4.0 * phase - 4.0))
+    return amplitude * tri
+
+
+def constant_protocol(V: float, n_steps: int) -> np.ndarray:
+    return np.full(n_steps, float(V), dtype=np.float64)
+
+
+# ------------------------------------------------------------ seeded inputs
+
+def random_occupancy(R: int, L: int, fill: float, seed: int) -> np.ndarray:
+    """Independent Bernoulli(fill) sites from numpy's PCG64 stream."""
+    rng = np.random.default_rng(seed)
+    return (rng.random((R, L)) < fill).astype(np.uint8)
+
+
+def normal_barriers(R: int, L: int, mean: float, sigma: float, seed: int) -> np.ndarray:
+    """Per-site migration barriers Ea ~ N(mean, sigma) in eV."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((R, L), dtype=np.float64)
+    rows = max(1, (1 << 22) // max(L, 1))
+    for r0 in range(0, R, rows):
+        r1 = min(R, r0 + rows)
+        out[r0:r1] = rng.normal(mean, sigma, size=(r1 - r0, L))
+    return out
+
+
+# ----------------------------------------------------------- named devices
+
+def relaxation_64x100(n_polarise: int = 5000, n_total: int = 10000) -> Workload:
+    """Plain single device: 64 rails x 100 sites, 800 ions placed uniformly
+    at random (seed 0), Ea = 0.40 eV, nu = 1e12 Hz, T = 300 K, d = 1 nm,
+    dt = 1e-9 s, 1 V for 5,000 steps then 0 V for 5,000 steps, blocking."""
+    dev = Device(R=64, L=100, Z=10, electrodes=0, seed=0)
+    return Workload("relaxation_64x100", dev,
+                    relaxation_protocol(n_polarise, 1.0, n_total, 0.0),
+                    init_mode=0, n_ions=800)
+
+
+def hysteresis_65536x1024(R: int = 65536, L: int = 1024, steps_per_cycle: int = 100000,
+                          cycles: int = 2, seed: int = 1, with_barriers: bool = True) -> Workload:
+    """Plain large device: 65,536 rails x 1,024 sites, 25 % filling,
+    Ea per site ~ N(0.40, 0.02) eV, T = 300 K, triangular sweep +-2 V at
+    1e5 steps per cycle for 2 cycles, injecting/extracting electrodes with
+    rate 1e9 Hz (reservoir density = the initial filling)."""
+    dev = Device(R=R, L=L, Z=10, electrodes=1, k_e=1e9, rho_e=0.25, seed=seed)
+    Ea = normal_barriers(R, L, 0.40, 0.02, seed + 1000) if with_barriers else None
+    return Workload("hysteresis_%dx%d" % (R, L), dev,
+                    triangle_protocol(2.0, steps_per_cycle, cycles),
+                    init_mode=1, fill=0.25, Ea_site=Ea)

@@ -1,0 +1,105 @@
+"""Shapes the paper validates, checked on the oracle (Sec. 4, Figs. 1-2;
+Supplementary S4, Figs. S1 and S3).  The paper prints no figure data, so the
+magnitudes are unpinned; only the qualitative trends it states are tested:
+
+- relaxation decay (Fig. 1): the decile-1 ion ratio grows with polarisation
+  voltage and time, linearly at low voltage and time, saturates at high
+  voltage, and decays monotonically toward a common value once the bias is off;
+- I-V hysteresis (Fig. 2, Fig. S3): faster sweeps give lower peak current and
+  narrower loops;
+- rails vs noise (S4.1): rails fluctuate independently, so the fluctuation of
+  the device signal falls as 1/sqrt(rails).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09413_gb300 import workloads as W
+
+
+def _dev(R, **kw):
+    d = dict(R=R, L=100, Z=10, electrodes=0, d=1.0, dt=5e-7, T=300.0, Ea=0.40, nu=1e12,
+             alpha=0.2, kappa=1.0, k_e=0.0, rho_e=0.0, seed=1, instance=0)
+    d.update(kw)
+    return d
+
+
+def _decile1_trace(dev, V, fill=0.3):
+    occ0 = oracle.init_occupancy(dev, 1, fill=fill)
+    sim = oracle.OracleSim(dev, V, occ0)
+    J, Zc = sim.step_n(len(V))
+    N = occ0.sum()
+    return Zc[:, 0] / N, Zc[:, -1] / N, J / N
+
+
+@pytest.fixture(scope="module")
+def relaxation_by_voltage():
+    out = {}
+    for Vp in (0.25, 0.5, 1.0, 2.0):
+        r, _, _ = _decile1_trace(_dev(256), W.relaxation_protocol(1000, Vp, 3500))
+        out[Vp] = r
+    return out
+
+
+def test_relaxation_grows_with_polarisation_voltage(relaxation_by_voltage):
+    r = relaxation_by_voltage
+    start = np.mean([r[v][:50].mean() for v in r])
+    at_removal = {v: r[v][950:1000].mean() for v in r}
+    vals = [at_removal[v] for v in sorted(r)]
+    assert all(a < b for a, b in zip(vals, vals[1:]))
+    gain = {v: at_removal[v] - start for v in r}
+    # linear response at moderate voltage ...
+    assert 1.6 < gain[0.5] / gain[0.25] < 2.4
+    # ... and saturation / Coulombic crowding at high voltage
+    assert gain[2.0] / gain[1.0] < 1.6
+
+
+def test_relaxation_decays_monotonically_toward_common_value(relaxation_by_voltage):
+    r = relaxation_by_voltage
+    for v in (0.5, 1.0, 2.0):
+        blocks = r[v][1000:3500].reshape(5, 500).mean(axis=1)
+        assert np.all(np.diff(blocks) < 0), (v, blocks)
+    # curves approach each other once the bias is off
+    gap_removal = r[2.0][950:1000].mean() - r[0.5][950:1000].mean()
+    gap_end = r[2.0][-200:].mean() - r[0.5][-200:].mean()
+    assert 0 < gap_end < 0.75 * gap_removal
+    # higher polarisation relaxes more slowly (still higher at the end)
+    ends = [r[v][-200:].mean() for v in sorted(r)]
+    assert all(a < b for a, b in zip(ends, ends[1:]))
+
+
+def test_relaxation_accumulation_linear_in_polarisation_time():
+    gains = {}
+    for npol in (250, 500):
+        r, _, _ = _decile1_trace(_dev(256, seed=4), W.relaxation_protocol(npol, 0.5, npol + 10))
+        gains[npol] = r[npol - 20:npol].mean() - r[:20].mean()
+    assert 1.6 < gains[500] / gains[250] < 2.4
+
+
+def _loop(steps_per_cycle, R=256, amp=1.0):
+    V = W.triangle_protocol(amp, steps_per_cycle, 2)
+    d1, d10, _ = _decile1_trace(_dev(R, seed=3), V)
+    # current (a.u.): decile 1 at V >= 0, decile 10 at V < 0 (Fig. 2 caption, S3)
+    I = np.where(V >= 0, d1, d10)
+    v, i = V[-steps_per_cycle:], I[-steps_per_cycle:]
+    area = abs(np.sum(0.5 * (i[1:] + i[:-1]) * np.diff(v)))
+    return i.max(), area
+
+
+def test_hysteresis_faster_sweeps_give_smaller_loops():
+    peak_slow, area_slow = _loop(2000)
+    peak_fast, area_fast = _loop(500)
+    peak_slowest, _ = _loop(8000)
+    assert peak_slowest > peak_slow > peak_fast
+    assert area_fast < area_slow
+    assert area_fast > 0.0
+
+
+def test_noise_falls_as_inverse_sqrt_rails():
+    def fluct(R):
+        _, _, j = _decile1_trace(_dev(R, seed=5), np.zeros(800))
+        r, _, _ = _decile1_trace(_dev(R, seed=5), np.zeros(800))
+        return np.diff(r).std(), j.std()
+    small, big = fluct(64), fluct(1024)
+    for a, b in zip(small, big):
+        assert 3.4 < a / b < 4.6     # sqrt(1024 / 64) = 4
