@@ -1,0 +1,149 @@
+/*
+ * kmc.h -- C ABI of the GB300 rail-based kinetic Monte Carlo ion-migration
+ * sweep (arXiv 2511.09413).
+ *
+ * One simulated device ("instance") is a lattice of n_rails independent rails
+ * of n_sites sites each (Supplementary S1.2, S2.1.1).  Every time step sweeps
+ * every rail and site (S2.1.2 - S2.1.7): zone counts, the space-charge field
+ * (S2.1.8), the energy gap of Eq. 3, the Boltzmann factor of Eq. 4, the hop
+ * probabilities of Eqs. 5-6 (with the base probability from Eq. 1), two
+ * uniforms per ion from a keyed Philox4x32-10 stream, exclusion, conflict
+ * cancellation, electrode exchange, and the net-crossing current.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: KMC_OK (0) on success, a negative KMC_E_* code otherwise.
+ *    No exception crosses this boundary.  kmc_last_error() returns a
+ *    human-readable message for the last failure on the calling thread.
+ *  - Host pointers are plain CPU memory owned by the caller; they are read or
+ *    written before the call returns unless stated otherwise.  Device memory
+ *    is owned by the handle.
+ *  - Occupancy layout: uint8 [n_rails][n_sites], row-major, values 0 or 1
+ *    (site 0 is next to the electrode the cations drift to at V > 0).
+ *  - Step indices are absolute: step t of a handle uses V[t] and Philox
+ *    counter word 2 = t; kmc_step_n continues from the handle's current step.
+ */
+#ifndef KMC_H
+#define KMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KMC_OK 0
+#define KMC_E_ARG (-1)     /* invalid argument (size, range, null pointer) */
+#define KMC_E_PROB (-2)    /* a derived probability is outside [0, 1] or not finite */
+#define KMC_E_NOMEM (-3)   /* device allocation failed */
+#define KMC_E_CUDA (-4)    /* a CUDA runtime call or kernel launch failed */
+#define KMC_E_TIMEOUT (-5) /* a bounded device-side wait gave up */
+#define KMC_E_RANGE (-6)   /* steps beyond the voltage table */
+
+#define KMC_MAX_SITES 2048
+#define KMC_MAX_ZONES 32
+
+/* Physical and numerical parameters of one device (one instance).
+ * Units: nm, s, K, eV, Hz, V.  See Table S1 for the paper's defaults. */
+typedef struct kmc_params {
+    int32_t n_rails;          /* R >= 1: rails (Table S1 dimension_y)                     */
+    int32_t n_sites;          /* L in [2, 2048]: sites per rail (Table S1 dimension_x)      */
+    int32_t n_zones;          /* Z in [1, min(L, 32)]: spatial zones (S2.1.5; paper uses 10)*/
+    int32_t electrodes;       /* 0 blocking, 1 injecting/extracting                         */
+    double site_spacing_nm;   /* d_hop of Eq. 3; the device thickness is t_dev = L d_hop     */
+    double dt_s;              /* time step                                                   */
+    double T_K;               /* temperature (Eqs. 1, 4)                                     */
+    double Ea_eV;             /* migration barrier of Eq. 1 (used when no per-site table)    */
+    double nu_Hz;             /* attempt frequency of Eq. 1                                  */
+    double alpha_V;           /* space-charge volts per excess ion on a rail (S2.1.8)       */
+    double kappa;             /* dimensionless space-charge coupling                         */
+    double k_electrode_Hz;    /* electrode exchange rate (electrodes == 1)                   */
+    double rho_electrode;     /* electrode reservoir density in [0, 1] (electrodes == 1)     */
+    uint64_t seed;            /* Philox key: (seed & 0xffffffff, seed >> 32)                 */
+    uint32_t instance;        /* Philox counter word 3                                       */
+    int32_t init_mode;        /* 0: n_ions ions on the sites with the smallest init keys;
+                                 1: Bernoulli(fill) per site; 2: caller occupancy            */
+    int64_t n_ions;           /* init_mode 0                                                 */
+    double fill;              /* init_mode 1                                                 */
+} kmc_params;
+
+/* One decision whose uniform fell within 1e-12 of its threshold. */
+typedef struct kmc_log_entry {
+    int32_t rail;
+    uint32_t step;
+    int32_t site;
+    int32_t dir;  /* 0 right trial, 1 left trial */
+    int32_t kind; /* 0 inner hop, 1 injection, 2 extraction */
+    int32_t pad;
+    double diff;  /* u - p */
+} kmc_log_entry;
+
+typedef struct kmc_handle kmc_handle;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` usable on `stream`, or NULL.
+ * free receives the pointer, its size and the stream it was used on.
+ * Passing NULL functions restores the default (cudaMallocAsync/cudaFreeAsync).
+ * Affects handles created afterwards.  Not thread-safe against kmc_create. */
+typedef void *(*kmc_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*kmc_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int kmc_set_allocator(kmc_alloc_fn alloc, kmc_free_fn free_fn, void *ctx);
+
+/* Create a device: validates parameters, allocates device state on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream), copies the
+ * voltage table V_per_step[n_steps_total] (S2.2: protocol as V(t) table),
+ * places ions (init_mode, S2.1.1; init_occ_or_null is read when init_mode is 2),
+ * and, if Ea_site_or_null is given (double [R][L], eV), uses a per-site
+ * barrier for hops leaving each site instead of Ea_eV.
+ * Errors: KMC_E_ARG for bad sizes or values, KMC_E_PROB if P0 or the electrode
+ * probabilities are not in [0, 1], KMC_E_NOMEM, KMC_E_CUDA.  On error *out is
+ * NULL and nothing is leaked.  Synchronizes the stream before returning. */
+int kmc_create(const kmc_params *params, const double *V_per_step, int64_t n_steps_total,
+               const uint8_t *init_occ_or_null, const double *Ea_site_or_null,
+               void *cuda_stream, kmc_handle **out);
+
+/* Advance n_steps >= 0 steps from the handle's current step (asynchronous on
+ * the handle's stream).  KMC_E_RANGE if the voltage table is too short. */
+int kmc_step_n(kmc_handle *h, int64_t n_steps);
+
+/* Read observables (synchronizes the stream):
+ *  J_out[count]            net leftward bond crossings per step, all rails and
+ *                          bonds including the electrode bonds (may be NULL);
+ *  zone_counts_out[count][Z] ions per zone at the start of each step, summed
+ *                          over rails (may be NULL);
+ *  occ_out_or_null[R][L]   current occupancy (may be NULL).
+ * Steps [first_step, first_step + count) must already have been simulated. */
+int kmc_observables(kmc_handle *h, int64_t first_step, int64_t count, int64_t *J_out,
+                    int64_t *zone_counts_out, uint8_t *occ_out_or_null);
+
+/* Overwrite V for steps [first_step, first_step + count) from host memory
+ * (asynchronous copy on the handle's stream; the host buffer must stay valid
+ * until the next synchronizing call). */
+int kmc_set_voltage(kmc_handle *h, int64_t first_step, int64_t count, const double *V_host);
+
+/* Copy up to `cap` near-threshold log entries (|u - p| < 1e-12) to `out` and
+ * report the total number logged in *n_total (synchronizes). */
+int kmc_near_threshold_log(kmc_handle *h, kmc_log_entry *out, int64_t cap, int64_t *n_total);
+
+/* Device counters since creation: [0] Philox blocks drawn, [1] decisions
+ * resolved by the exact FP64 path, [2] accepted moves (synchronizes). */
+int kmc_counters(kmc_handle *h, uint64_t out[3]);
+
+/* Launch shape: warps per CTA (1..32, 0 = automatic) and steps between
+ * trace flushes (1..1024, 0 = automatic).  Results do not depend on either. */
+int kmc_set_launch(kmc_handle *h, int warps_per_cta, int flush_steps);
+
+/* Current absolute step of the handle. */
+int64_t kmc_current_step(const kmc_handle *h);
+
+/* Release all device memory of the handle (synchronizes its stream). */
+void kmc_destroy(kmc_handle *h);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *kmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMC_H */

@@ -203,11 +203,13 @@ static uint64_t init_key(const orc_params *P, uint32_t site, uint32_t rail)
     return ((uint64_t)x[1] << 32) | x[0];
 }
 
-int orc_init_occupancy(const orc_params *P, int mode, int64_t n_ions, double fill, uint8_t *occ)
+int orc_init_occupancy(const orc_params *P, int mode, int64_t n_ions, double fill,
+                       const int32_t *rail_ids, uint8_t *occ)
 {
     const int R = P->R, L = P->L;
     const int64_t n = (int64_t)R * L;
     if (mode == 0) {
+        if (rail_ids) return -1; /* the exact count is defined over the whole device */
         /* exactly n_ions ions on the sites with the smallest init keys */
         if (n_ions < 0 || n_ions > n) return -1;
         orc_keyed *all = (orc_keyed *)malloc((size_t)n * sizeof(orc_keyed));
@@ -227,7 +229,8 @@ int orc_init_occupancy(const orc_params *P, int mode, int64_t n_ions, double fil
         /* independent Bernoulli(fill) per site */
         for (int r = 0; r < R; ++r)
             for (int k = 0; k < L; ++k) {
-                double u = (double)(init_key(P, (uint32_t)k, (uint32_t)r) >> 11) * 0x1.0p-53;
+                uint32_t rail = rail_ids ? (uint32_t)rail_ids[r] : (uint32_t)r;
+                double u = (double)(init_key(P, (uint32_t)k, rail) >> 11) * 0x1.0p-53;
                 occ[(int64_t)r * L + k] = (u < fill) ? 1 : 0;
             }
         return 0;
@@ -365,8 +368,9 @@ static void rail_step(const orc_params *P, int r, uint32_t t, double V, uint8_t 
 }
 
 int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, uint8_t *occ,
-            const int32_t *N0, const double *P0site, int64_t *J_out, int64_t *Zc_out,
-            int64_t *J_rail, orc_log_entry *log, int64_t log_cap, int64_t *log_count, int nthreads)
+            const int32_t *N0, const double *P0site, const int32_t *rail_ids, int64_t *J_out,
+            int64_t *Zc_out, int64_t *J_rail, orc_log_entry *log, int64_t log_cap,
+            int64_t *log_count, int nthreads)
 {
     const int R = P->R, L = P->L, Z = P->Z;
     if (L < 2 || Z < 1 || Z > ORC_MAX_ZONES || Z > L || R < 0) return -1;
@@ -397,7 +401,8 @@ int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, u
 #endif
             for (int r = 0; r < R; ++r) {
                 int64_t Jr = 0;
-                rail_step(P, r, t, V[t], occ + (int64_t)r * L, N0[r],
+                const int rail = rail_ids ? rail_ids[r] : r;
+                rail_step(P, rail, t, V[t], occ + (int64_t)r * L, N0[r],
                           P0site ? P0site + (int64_t)r * L : NULL, P0scalar, E_in, E_out,
                           mvR, mvL, next, &Jr, zc, log, log_cap, log_count);
                 J += Jr;

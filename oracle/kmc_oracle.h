@@ -50,11 +50,15 @@ void orc_p0_table(const orc_params *P, const double *Ea_site, double *P0);
 void orc_hop_probs(double base, double B, double inv, double *p_left, double *p_right);
 void orc_zone_field(const orc_params *P, const int32_t *Nz, int32_t N0, double V, double *dV,
                     double *B, double *inv);
-int orc_init_occupancy(const orc_params *P, int mode, int64_t n_ions, double fill, uint8_t *occ);
+/* rail_ids (optional, Bernoulli mode only): global rail index of each local rail */
+int orc_init_occupancy(const orc_params *P, int mode, int64_t n_ions, double fill,
+                       const int32_t *rail_ids, uint8_t *occ);
+/* rail_ids (optional): global rail index (Philox counter word 1) of each local
+ * rail, so that a sample of a large device can be advanced on its own */
 int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, uint8_t *occ,
-            const int32_t *N0, const double *P0site, int64_t *J_out, int64_t *Zc_out,
-            int64_t *J_rail, orc_log_entry *log, int64_t log_cap, int64_t *log_count,
-            int nthreads);
+            const int32_t *N0, const double *P0site, const int32_t *rail_ids, int64_t *J_out,
+            int64_t *Zc_out, int64_t *J_rail, orc_log_entry *log, int64_t log_cap,
+            int64_t *log_count, int nthreads);
 int orc_max_threads(void);
 
 #endif

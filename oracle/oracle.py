@@ -84,10 +84,11 @@ def lib():
         L.orc_p0_table.argtypes = [P, f64p, f64p]
         L.orc_hop_probs.argtypes = [ctypes.c_double] * 3 + [f64p, f64p]
         L.orc_zone_field.argtypes = [P, i32p, ctypes.c_int32, ctypes.c_double, f64p, f64p, f64p]
-        L.orc_init_occupancy.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_double, u8p]
+        L.orc_init_occupancy.argtypes = [P, ctypes.c_int, ctypes.c_int64, ctypes.c_double, i32p,
+                                         u8p]
         L.orc_init_occupancy.restype = ctypes.c_int
-        L.orc_run.argtypes = [P, f64p, ctypes.c_int64, ctypes.c_int64, u8p, i32p, f64p, i64p,
-                              i64p, i64p, ctypes.POINTER(OrcLogEntry), ctypes.c_int64, i64p,
+        L.orc_run.argtypes = [P, f64p, ctypes.c_int64, ctypes.c_int64, u8p, i32p, f64p, i32p,
+                              i64p, i64p, i64p, ctypes.POINTER(OrcLogEntry), ctypes.c_int64, i64p,
                               ctypes.c_int]
         L.orc_run.restype = ctypes.c_int
         L.orc_max_threads.restype = ctypes.c_int
@@ -169,11 +170,17 @@ def zone_field(dev, Nz, N0: int, V: float):
     return dV, B, inv
 
 
-def init_occupancy(dev, mode: int, n_ions: int = 0, fill: float = 0.0) -> np.ndarray:
+def init_occupancy(dev, mode: int, n_ions: int = 0, fill: float = 0.0,
+                   rail_ids: Optional[np.ndarray] = None) -> np.ndarray:
+    """Initial placement; with rail_ids (Bernoulli only) the rows are those
+    global rails of the device, so P.R must equal len(rail_ids)."""
     P = params(dev)
+    ids = None if rail_ids is None else np.ascontiguousarray(rail_ids, dtype=np.int32)
+    if ids is not None:
+        P.R = len(ids)
     occ = np.zeros((P.R, P.L), dtype=np.uint8)
     rc = lib().orc_init_occupancy(ctypes.byref(P), int(mode), int(n_ions), float(fill),
-                                  _ptr(occ, ctypes.c_uint8))
+                                  _ptr(ids, ctypes.c_int32), _ptr(occ, ctypes.c_uint8))
     if rc != 0:
         raise ValueError("orc_init_occupancy failed (%d)" % rc)
     return occ
@@ -189,13 +196,23 @@ class OracleSim:
     """Oracle state of one device: occupancy, N0 per rail, step counter."""
 
     def __init__(self, dev, V: np.ndarray, occ0: np.ndarray, Ea_site: Optional[np.ndarray] = None,
-                 log_cap: int = 4096, nthreads: int = 0):
+                 log_cap: int = 4096, nthreads: int = 0, rail_ids: Optional[np.ndarray] = None):
+        """rail_ids: global rail index of each row of occ0 (a sample of a larger
+        device); by default row r is rail r."""
         self.dev = dev
         self.P = params(dev)
+        self.rail_ids = None if rail_ids is None else np.ascontiguousarray(rail_ids, dtype=np.int32)
+        if self.rail_ids is not None:
+            self.P.R = len(self.rail_ids)
         self.V = np.ascontiguousarray(V, dtype=np.float64)
         self.occ = np.ascontiguousarray(occ0, dtype=np.uint8).reshape(self.P.R, self.P.L).copy()
         self.N0 = self.occ.sum(axis=1).astype(np.int32)
-        self.P0site = p0_table(dev, Ea_site) if Ea_site is not None else None
+        self.P0site = None
+        if Ea_site is not None:
+            Ea = np.ascontiguousarray(Ea_site, dtype=np.float64).reshape(self.P.R, self.P.L)
+            self.P0site = np.empty_like(Ea)
+            lib().orc_p0_table(ctypes.byref(self.P), _ptr(Ea, ctypes.c_double),
+                               _ptr(self.P0site, ctypes.c_double))
         self.t = 0
         self.J_rail = np.zeros(self.P.R, dtype=np.int64)
         self.log = np.zeros(log_cap, dtype=LOG_DTYPE)
@@ -218,7 +235,8 @@ class OracleSim:
         Zc = np.zeros((n, P.Z), dtype=np.int64)
         rc = lib().orc_run(ctypes.byref(P), _ptr(self.V, ctypes.c_double), self.t, n,
                            _ptr(self.occ, ctypes.c_uint8), _ptr(self.N0, ctypes.c_int32),
-                           _ptr(self.P0site, ctypes.c_double), _ptr(J, ctypes.c_int64),
+                           _ptr(self.P0site, ctypes.c_double), _ptr(self.rail_ids, ctypes.c_int32),
+                           _ptr(J, ctypes.c_int64),
                            _ptr(Zc, ctypes.c_int64), _ptr(self.J_rail, ctypes.c_int64),
                            self.log.ctypes.data_as(ctypes.POINTER(OrcLogEntry)),
                            len(self.log), _ptr(self.log_count, ctypes.c_int64), self.nthreads)

@@ -1,0 +1,93 @@
+// kmc_internal.h -- device-side data structures shared by the kernels
+// (kmc_sweep.cu, kmc_setup.cu) and the host runtime (kmc_capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kmc.h"
+
+namespace kmc {
+
+constexpr uint32_t kInitStep = 0xFFFFFFFFu;   // Philox step word of the placement stream
+constexpr int kMaxZones = KMC_MAX_ZONES;
+constexpr int kMaxSites = KMC_MAX_SITES;
+
+// Per-device constants derived from kmc_params on the device (setup kernel):
+// exact FP64 values used by the exact decision path and their FP32 images
+// used by the bounded fast path.
+struct DevConst {
+    double P0;      // -expm1(-2 Gamma0 dt), Gamma0 = nu exp(-Ea / kT)   (Eq. 1)
+    double E_in;    // E rho_e,        E = -expm1(-2 k_e dt)
+    double E_out;   // E (1 - rho_e)
+    double ka;      // kappa * alpha
+    double kT;      // k_B T, k_B = 8.6173e-5 eV/K (Eq. 4)
+    double d;       // hop distance
+    double t_dev;   // L d
+    float P0f, E_inf, E_outf, pad;
+    int32_t status; // 0 ok, else a KMC_E_* code found while deriving
+    int32_t pad2;
+    int32_t bnd[kMaxZones + 1];  // zone boundaries floor(z L / Z), z = 0..Z
+};
+
+// Everything one sweep launch needs.  Passed by value (kernel parameter space).
+struct SweepArgs {
+    uint8_t *occ;              // [R][stride] occupancy bytes
+    int64_t stride;            // bytes per rail (L rounded up to 16)
+    int32_t R, L, Z, electrodes;
+    uint32_t instance;
+    uint32_t rk0[10], rk1[10]; // Philox round keys (seed words plus Weyl increments)
+    int64_t t0;                // absolute step of the first step of this launch
+    int32_t n_steps;
+    int32_t flush;             // steps between trace flushes
+    const double *V;           // [n_steps_total]
+    const int32_t *N0;         // [R] background (initial) ion count per rail
+    const double *P0site;      // [R][L] or null
+    const float2 *P0bnd;       // [R][Z] (min, max) of P0site over the zone, or null
+    const DevConst *K;
+    unsigned long long *J;     // [n_steps_total] int64 two's complement
+    unsigned long long *Zc;    // [n_steps_total][Z]
+    kmc_log_entry *log;
+    unsigned long long *log_count;
+    int64_t log_cap;
+    unsigned long long *counters; // [3] philox blocks, exact decisions, moves
+    int32_t bnd[kMaxZones + 1];   // zone boundaries floor(z L / Z)
+    int32_t wsum[kMaxZones + 1];  // w_{z-1} + w_z (w_{-1} = w_Z = 0)
+    float cz[kMaxZones];          // ((b_z + b_{z+1}) - H / L) / (2 L), H = sum w_z (b_z + b_{z+1})
+    float inv_L;                  // 1 / L
+    float inv_LkT;                // 1 / (L kT)
+    float ka_f;                   // kappa alpha
+    float delta;                  // relative half-width of the FP32 probability band
+};
+
+// Launch configuration chosen on the host.
+struct SweepLaunch {
+    int lpr;      // lanes per rail (1..32)
+    int wpl;      // 32-bit words per lane (1 or 2)
+    int warps;    // warps per CTA
+    size_t smem;  // dynamic shared memory bytes
+    int grid;
+};
+
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush);
+int sweep_pick_lpr(int L, int *wpl);
+cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
+cudaError_t sweep_set_smem_limits();
+
+// setup kernels (kmc_setup.cu)
+cudaError_t setup_constants(const kmc_params &p, DevConst *K, cudaStream_t s);
+cudaError_t setup_p0_table(const kmc_params &p, const double *Ea, double *P0, int64_t n, int *bad,
+                           cudaStream_t s);
+cudaError_t setup_p0_bounds(const double *P0, int32_t R, int32_t L, int32_t Z, const DevConst *K,
+                            float2 *out, cudaStream_t s);
+cudaError_t setup_row_counts(const uint8_t *occ, int64_t stride, int32_t R, int32_t L,
+                             int32_t *N0, unsigned long long *bad, cudaStream_t s);
+cudaError_t setup_init_bernoulli(const kmc_params &p, uint8_t *occ, int64_t stride,
+                                 cudaStream_t s);
+// mode 0: count init keys <= key_bound; mode 1: keys == key_bound with linear index <= idx_bound
+cudaError_t setup_count_keys(const kmc_params &p, uint64_t key_bound, int mode, int64_t idx_bound,
+                             unsigned long long *count, cudaStream_t s);
+cudaError_t setup_mark_smallest(const kmc_params &p, uint64_t key_star, int64_t idx_star,
+                                int select_none, uint8_t *occ, int64_t stride, cudaStream_t s);
+
+}  // namespace kmc

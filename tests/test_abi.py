@@ -1,0 +1,109 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry point
+include/kmc.h declares, the ctypes structures match the C layout, and host-side
+argument validation rejects bad input before touching a GPU."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kmc.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(kmc_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2511_09413_gb300 import build, kmc
+    build.build()
+    return kmc.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("kmc_create", "kmc_step_n", "kmc_observables", "kmc_destroy", "kmc_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2511_09413_gb300 import kmc
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert sorted(kmc.EXPORTS) == _declared()
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_2511_09413_gb300 import kmc
+    # kmc_params: 4 int32, 9 double, uint64, uint32, int32, int64, double
+    assert ctypes.sizeof(kmc.kmc_params) == 4 * 4 + 9 * 8 + 8 + 4 + 4 + 8 + 8
+    assert kmc.kmc_params.seed.offset == 16 + 72
+    assert ctypes.sizeof(kmc.kmc_log_entry) == 32
+    assert kmc.LOG_DTYPE.itemsize == 32
+
+
+def _params(**kw):
+    from paper_2511_09413_gb300 import kmc
+    d = dict(n_rails=4, n_sites=100, n_zones=10, electrodes=0, site_spacing_nm=1.0, dt_s=1e-9,
+             T_K=300.0, Ea_eV=0.4, nu_Hz=1e12, alpha_V=0.2, kappa=1.0, k_electrode_Hz=0.0,
+             rho_electrode=0.0, seed=0, instance=0, init_mode=1, n_ions=0, fill=0.25)
+    d.update(kw)
+    return kmc.kmc_params(**d)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_rails=0), dict(n_sites=1), dict(n_sites=4096), dict(n_zones=0), dict(n_zones=33),
+    dict(n_sites=8, n_zones=9), dict(electrodes=2), dict(dt_s=0.0), dict(T_K=-1.0),
+    dict(site_spacing_nm=float("nan")), dict(nu_Hz=-1.0), dict(init_mode=3),
+    dict(init_mode=1, fill=1.5), dict(init_mode=0, n_ions=401), dict(init_mode=2),
+    dict(electrodes=1, rho_electrode=1.5), dict(kappa=float("inf")),
+])
+def test_validation_rejects_bad_parameters_on_host(lib, bad):
+    from paper_2511_09413_gb300 import kmc
+    p = _params(**bad)
+    V = np.zeros(10)
+    h = ctypes.c_void_p()
+    rc = lib.kmc_create(ctypes.byref(p), V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 10,
+                        None, None, None, ctypes.byref(h))
+    assert rc == kmc.KMC_E_ARG
+    assert h.value is None
+    assert len(lib.kmc_last_error()) > 0
+
+
+def test_validation_rejects_non_finite_voltage(lib):
+    from paper_2511_09413_gb300 import kmc
+    p = _params()
+    V = np.array([0.0, np.nan, 1.0])
+    h = ctypes.c_void_p()
+    rc = lib.kmc_create(ctypes.byref(p), V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 3,
+                        None, None, None, ctypes.byref(h))
+    assert rc == kmc.KMC_E_ARG
+    assert b"not finite" in lib.kmc_last_error()
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2511_09413_gb300 import kmc
+    assert lib.kmc_step_n(None, 1) == kmc.KMC_E_ARG
+    assert lib.kmc_observables(None, 0, 0, None, None, None) == kmc.KMC_E_ARG
+    assert lib.kmc_current_step(None) == -1
+    lib.kmc_destroy(None)
+
+
+def test_missing_library_raises(tmp_path):
+    from paper_2511_09413_gb300 import kmc
+    saved = kmc._lib
+    kmc._lib = None
+    try:
+        with pytest.raises(ImportError):
+            kmc.load(str(tmp_path / "libkmc.so"))
+    finally:
+        kmc._lib = saved

@@ -1,0 +1,201 @@
+"""GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Occupancy trajectories, per-step current and zone counts
+must be bit-identical; integer traces leave no room for tolerance.  Near-
+threshold decisions (|u - p| < 1e-12) must be logged identically."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09413_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kmc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_09413_gb300 import build, kmc as K
+    build.build()
+    K.load()
+    torch.cuda.init()
+    return K
+
+
+def _dev(**kw):
+    d = dict(R=8, L=100, Z=10, electrodes=0, d=1.0, dt=5e-7, T=300.0, Ea=0.40, nu=1e12,
+             alpha=0.2, kappa=1.0, k_e=0.0, rho_e=0.0, seed=7, instance=0)
+    d.update(kw)
+    return d
+
+
+def _compare(kmc, dev, V, occ0, Ea=None, chunks=None, warps=0, flush=0):
+    """Run GPU and oracle from the same occupancy; compare everything."""
+    n = len(V)
+    sim = kmc.Sim(dev, V, init_mode=2, occ0=occ0, Ea_site=Ea)
+    if warps or flush:
+        sim.set_launch(warps, flush)
+    orc = oracle.OracleSim(dev, V, occ0, Ea)
+    for c in (chunks or [n]):
+        sim.step_n(c)
+    Jo, Zo = orc.step_n(n)
+    Jg, Zg = sim.traces()
+    occ_g = sim.occupancy()
+    assert np.array_equal(Zg, Zo), "zone-count traces differ"
+    assert np.array_equal(Jg, Jo), "current traces differ"
+    assert np.array_equal(occ_g, orc.occ), "final occupancy differs"
+    lg, lo = sim.near_threshold_log(), orc.near_threshold_log()
+    assert len(lg) == len(lo)
+    cnt = sim.counters()
+    sim.close()
+    return Jg, Zg, occ_g, cnt
+
+
+def test_relaxation_64x100_full_run_bit_exact(kmc):
+    """64 rails x 100 sites, 800 ions at seed 0, 1 V x 5000 then 0 V x 5000."""
+    wl = W.relaxation_64x100()
+    sim = kmc.Sim.from_workload(wl)
+    orc = oracle.OracleSim.from_workload(wl)
+    assert np.array_equal(sim.occupancy(), orc.occ), "initial placement differs"
+    assert sim.occupancy().sum() == 800
+    sim.step_n(5000)
+    sim.step_n(5000)
+    Jo, Zo = orc.step_n(10000)
+    Jg, Zg = sim.traces()
+    assert np.array_equal(Zg, Zo)
+    assert np.array_equal(Jg, Jo)
+    assert np.array_equal(sim.occupancy(), orc.occ)
+    assert len(sim.near_threshold_log()) == len(orc.near_threshold_log())
+    sim.close()
+
+
+@pytest.mark.parametrize("L", [2, 3, 5, 31, 32, 33, 37, 64, 100, 127, 128, 129, 255, 500, 1000,
+                               1023, 1024, 1025, 1500, 2047, 2048])
+@pytest.mark.parametrize("electrodes", [0, 1])
+def test_shapes_bit_exact(kmc, L, electrodes):
+    rng = np.random.default_rng(L * 3 + electrodes)
+    Z = int(min(L, [1, 3, 10, 32][L % 4]))
+    R = int(rng.integers(1, 41))
+    dev = _dev(R=R, L=L, Z=Z, electrodes=electrodes, k_e=2e6 if electrodes else 0.0,
+               rho_e=0.3 if electrodes else 0.0, seed=int(rng.integers(0, 2 ** 63)),
+               instance=int(rng.integers(0, 1000)))
+    occ0 = W.random_occupancy(R, L, float(rng.uniform(0.05, 0.7)), seed=L)
+    V = W.triangle_protocol(3.0, 150, 2)
+    _compare(kmc, dev, V, occ0)
+
+
+@pytest.mark.parametrize("L,electrodes", [(100, 0), (1024, 1), (2048, 1), (37, 1)])
+def test_per_site_barriers_bit_exact(kmc, L, electrodes):
+    R = 24
+    dev = _dev(R=R, L=L, electrodes=electrodes, k_e=1e6, rho_e=0.25, seed=99)
+    occ0 = W.random_occupancy(R, L, 0.3, seed=5)
+    Ea = W.normal_barriers(R, L, 0.40, 0.02, seed=6)
+    V = W.triangle_protocol(2.0, 200, 2)
+    _compare(kmc, dev, V, occ0, Ea=Ea)
+
+
+def test_chunked_steps_and_launch_shapes_identical(kmc):
+    dev = _dev(R=50, L=300, Z=7, electrodes=1, k_e=3e6, rho_e=0.4)
+    occ0 = W.random_occupancy(50, 300, 0.35, seed=1)
+    V = W.triangle_protocol(4.0, 97, 3)
+    a = _compare(kmc, dev, V, occ0)
+    b = _compare(kmc, dev, V, occ0, chunks=[1, 2, 30, 100, len(V) - 133], warps=2, flush=7)
+    c = _compare(kmc, dev, V, occ0, warps=1, flush=1)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    for x, y in zip(a[:3], c[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_strong_space_charge_and_large_bias(kmc):
+    # large |exponent| drives decisions through the exact FP64 path
+    dev = _dev(R=16, L=200, Z=10, alpha=3.0, kappa=1.0, electrodes=1, k_e=1e7, rho_e=0.9)
+    occ0 = W.random_occupancy(16, 200, 0.6, seed=3)
+    V = np.concatenate([np.full(200, 60.0), np.full(200, -60.0), np.zeros(100)])
+    _, _, _, cnt = _compare(kmc, dev, V, occ0)
+    assert cnt[1] > 0   # some decisions needed the exact path
+
+
+def test_empty_and_full_rails(kmc):
+    for fill in (0.0, 1.0):
+        for electrodes in (0, 1):
+            dev = _dev(R=9, L=70, electrodes=electrodes, k_e=5e6, rho_e=0.5)
+            occ0 = np.full((9, 70), int(fill), dtype=np.uint8)
+            _compare(kmc, dev, W.constant_protocol(1.0, 120), occ0)
+
+
+def test_zero_steps_and_range_errors(kmc):
+    dev = _dev(R=3, L=40)
+    sim = kmc.Sim(dev, np.zeros(10), init_mode=1, fill=0.5)
+    sim.step_n(0)
+    assert sim.t == 0
+    sim.step_n(10)
+    with pytest.raises(kmc.KmcError) as e:
+        sim.step_n(1)
+    assert e.value.code == kmc.KMC_E_RANGE
+    with pytest.raises(kmc.KmcError):
+        sim.traces(5, 10)
+    sim.close()
+
+
+@pytest.mark.parametrize("R,L,fill", [(64, 100, 0.25), (1000, 1024, 0.25), (3, 2048, 0.9)])
+def test_bernoulli_placement_bit_exact(kmc, R, L, fill):
+    dev = _dev(R=R, L=L)
+    sim = kmc.Sim(dev, np.zeros(1), init_mode=1, fill=fill)
+    assert np.array_equal(sim.occupancy(), oracle.init_occupancy(dev, 1, fill=fill))
+    sim.close()
+
+
+@pytest.mark.parametrize("R,L,n", [(64, 100, 800), (5, 37, 0), (5, 37, 185), (7, 300, 1),
+                                   (300, 64, 5000)])
+def test_exact_count_placement_bit_exact(kmc, R, L, n):
+    dev = _dev(R=R, L=L)
+    sim = kmc.Sim(dev, np.zeros(1), init_mode=0, n_ions=n)
+    got = sim.occupancy()
+    assert got.sum() == n
+    assert np.array_equal(got, oracle.init_occupancy(dev, 0, n_ions=n))
+    sim.close()
+
+
+def test_near_threshold_decision_logged(kmc):
+    dev = dict(R=1, L=5, Z=1, electrodes=0, d=1.0, dt=1e-6, T=300.0, Ea=0.0, nu=1e12,
+               alpha=0.0, kappa=0.0, k_e=0.0, rho_e=0.0, seed=42, instance=0)
+    for rail in range(64):
+        x = oracle.philox4x32_10([2, rail, 0, 0], [42, 0])
+        uL = float(((int(x[3]) << 32) | int(x[2])) >> 11) * 2.0 ** -53
+        if 0.05 < uL < 0.45:
+            break
+    dev["nu"] = -np.log1p(-2.0 * uL) / (2.0 * dev["dt"])
+    dev["R"] = rail + 1
+    occ0 = np.tile(np.array([0, 0, 1, 0, 0], dtype=np.uint8), (rail + 1, 1))
+    sim = kmc.Sim(dev, np.zeros(1), init_mode=2, occ0=occ0)
+    sim.step_n(1)
+    log = [e for e in sim.near_threshold_log() if e["rail"] == rail]
+    assert len(log) == 1
+    assert (log[0]["step"], log[0]["site"], log[0]["dir"], log[0]["kind"]) == (0, 2, 1, 0)
+    assert abs(log[0]["diff"]) < 1e-12
+    sim.close()
+
+
+def test_hysteresis_device_sampled_rails_full_size(kmc):
+    """65,536 x 1,024 device, per-site barriers, open electrodes, +-2 V sweep:
+    the GPU advances the whole device; every 256th rail is re-run on the
+    oracle (rails are independent and keyed by their index) and must match."""
+    wl = W.hysteresis_65536x1024(steps_per_cycle=100000, cycles=2)
+    n = 300
+    sim = kmc.Sim.from_workload(wl)
+    occ_init = sim.occupancy()
+    ids = np.arange(0, wl.device.R, 256)
+    assert np.array_equal(occ_init[ids], oracle.init_occupancy(wl.device, 1, fill=wl.fill,
+                                                               rail_ids=ids))
+    sim.step_n(n)
+    Jg, Zg = sim.traces()
+    occ_g = sim.occupancy()
+    orc = oracle.OracleSim(wl.device, wl.V, occ_init[ids], wl.Ea_site[ids], rail_ids=ids)
+    orc.step_n(n)
+    assert np.array_equal(occ_g[ids], orc.occ)
+    # the first zone-count row is the initial occupancy summed per zone
+    z = np.array([oracle.zone_of(k, wl.device.L, wl.device.Z) for k in range(wl.device.L)])
+    assert np.array_equal(Zg[0], np.bincount(z, weights=occ_init.sum(axis=0), minlength=10))
+    sim.close()

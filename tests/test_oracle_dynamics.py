@@ -228,3 +228,21 @@ def test_near_threshold_decisions_are_logged():
     e = hits[0]
     assert (e["step"], e["site"], e["dir"], e["kind"]) == (0, 2, 1, 0)
     assert abs(e["diff"]) < 1e-12
+
+
+def test_rail_sample_matches_full_device():
+    # a sample of rails advanced on its own (rail index map) equals those rows
+    # of the whole device: rails are independent and keyed by their index
+    dev = dict(R=20, L=48, Z=6, electrodes=1, d=1.0, dt=5e-7, T=300.0, Ea=0.40, nu=1e12,
+               alpha=0.2, kappa=1.0, k_e=1e6, rho_e=0.25, seed=11, instance=3)
+    V = np.linspace(1.5, -1.5, 300)
+    occ0 = oracle.init_occupancy(dev, 1, fill=0.3)
+    ids = np.array([5, 17, 0, 19])
+    assert np.array_equal(oracle.init_occupancy(dev, 1, fill=0.3, rail_ids=ids), occ0[ids])
+    Ea = 0.40 + 0.02 * np.random.default_rng(2).standard_normal((20, 48))
+    full = oracle.OracleSim(dev, V, occ0, Ea)
+    full.step_n(300)
+    part = oracle.OracleSim(dev, V, occ0[ids], Ea[ids], rail_ids=ids)
+    part.step_n(300)
+    assert np.array_equal(part.occ, full.occ[ids])
+    assert np.array_equal(part.J_rail, full.J_rail[ids])
