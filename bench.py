@@ -1,0 +1,325 @@
+"""Benchmark of the rail-based KMC sweep on GB300 (site-updates/s).
+
+Workload (N=1): the plain large device -- 65,536 rails x 1,024 sites (64 MiB
+uint8 occupancy), 25 % Bernoulli filling, per-site barriers Ea ~ N(0.40, 0.02)
+eV, T = 300 K, injecting/extracting electrodes (1e9 Hz), triangular +-2 V sweep
+with 1e5 steps per cycle.  One benchmark step = one kmc_step_n call advancing
+every rail and site by `--chunk` time steps (default 1,000), so one step is
+R * L * chunk site-updates.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kmc|reference]
+
+Under torchrun (N > 1) every rank advances its own independent device instance
+(instance = rank, weak scaling, no collective on the data path); the timed
+region is bracketed by a barrier and the maximum over ranks is reported.
+``--impl reference`` times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same device (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2511_09413_gb300 import workloads as W  # noqa: E402
+
+METRIC = "site-updates/s on 1 GB300 (% HBM roofline)"
+UNIT = "site-updates/s"
+BYTES_PER_SITE_UPDATE = 2.0        # uint8 read + write per site and step
+PHILOX_IMAD = 40                   # IMAD-pipe ops per Philox4x32-10 block: 20 products x (hi, lo)
+IMAD_PER_SM_PER_CLK = 64           # 32-bit integer multiply-add lanes per SM per clock
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured", float(d.get("sm_max_mhz", SM_MAX_MHZ))
+    except Exception:
+        return 6800.0, "fallback", SM_MAX_MHZ
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _voltage(n_needed: int, steps_per_cycle: int = 100000) -> np.ndarray:
+    cycles = max(2, -(-n_needed // steps_per_cycle))
+    return W.triangle_protocol(2.0, steps_per_cycle, cycles)
+
+
+def cpu_baseline(wl, budget_s: float, stride: int = 16, steps_per_call: int = 25):
+    """Time the FP64 oracle, as it stands, on this host's cores on every
+    `stride`-th rail of the device for about `budget_s` seconds."""
+    import oracle
+    ids = np.arange(0, wl.device.R, stride, dtype=np.int32)
+    occ0 = oracle.init_occupancy(wl.device, 1, fill=wl.fill, rail_ids=ids)
+    Ea = wl.Ea_site[ids] if wl.Ea_site is not None else None
+    sim = oracle.OracleSim(wl.device, wl.V, occ0, Ea, rail_ids=ids)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step_n(steps_per_call)
+        steps += steps_per_call
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    su = len(ids) * wl.device.L * steps
+    return {"value": su / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d of %d rails (every %dth) x %d steps of %s, %.1f s" % (
+                len(ids), wl.device.R, stride, steps, wl.name, el)}
+
+
+def run_reference(args):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n_needed = (args.warmup + args.steps) * args.ref_steps
+    wl = W.hysteresis_65536x1024(R=args.rails, steps_per_cycle=100000, cycles=2)
+    wl.V = _voltage(n_needed)
+    ids = np.arange(0, wl.device.R, args.ref_stride, dtype=np.int32)
+    occ0 = oracle.init_occupancy(wl.device, 1, fill=wl.fill, rail_ids=ids)
+    Ea = wl.Ea_site[ids] if wl.Ea_site is not None else None
+    sim = oracle.OracleSim(wl.device, wl.V, occ0, Ea, rail_ids=ids)
+    for _ in range(args.warmup):
+        sim.step_n(args.ref_steps)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sim.step_n(args.ref_steps)
+        times.append(time.perf_counter() - t0)
+    su_step = len(ids) * wl.device.L * args.ref_steps
+    total = sum(times)
+    value = su_step * args.steps / total
+    sample = "%d of %d rails (every %dth) x %d time steps per step" % (
+        len(ids), wl.device.R, args.ref_stride, args.ref_steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "rails": wl.device.R, "sites": wl.device.L,
+                   "sample": sample, "parallelism": "OpenMP over rails (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_kmc(args):
+    import torch
+    from paper_2511_09413_gb300 import kmc
+
+    rank, local_rank, world = _env_rank()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    kmc.load()
+    stream = torch.cuda.current_stream()
+    n_needed = (args.warmup + args.steps) * args.chunk + 2 * args.chunk
+    wl = W.hysteresis_65536x1024(R=args.rails, steps_per_cycle=100000, cycles=2)
+    wl.V = _voltage(n_needed)
+    wl.device.instance = rank
+    sim = kmc.Sim.from_workload(wl, stream=stream.cuda_stream)
+    R, L = wl.device.R, wl.device.L
+    su_per_step = R * L * args.chunk
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        sim.step_n(args.chunk)
+    torch.cuda.synchronize()
+    cnt0 = sim.counters()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush_buf.zero_()                         # evict L2 between timed steps
+        ev[i][0].record(stream)
+        sim.step_n(args.chunk)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(ms_steps)
+    cnt1 = sim.counters()
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * su_per_step * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: voltage chunk in, traces out
+    from paper_2511_09413_gb300.kmc import kmc_observables, kmc_set_voltage
+    Vpin = torch.empty(args.chunk, dtype=torch.float64, pin_memory=True).numpy()
+    Jpin = torch.empty(args.chunk, dtype=torch.int64, pin_memory=True).numpy()
+    Zpin = torch.empty((args.chunk, wl.device.Z), dtype=torch.int64, pin_memory=True).numpy()
+    e2e_steps = max(1, min(args.steps, 5))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        first = sim.t
+        Vpin[:] = wl.V[first:first + args.chunk]
+        kmc_set_voltage(sim.h, first, Vpin)
+        sim.step_n(args.chunk)
+        kmc_observables(sim.h, first, args.chunk, Jpin, Zpin, None)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * su_per_step * e2e_steps / e2e_s
+
+    if rank == 0:
+        hbm, hbm_src, sm_max = _peaks()
+        draws = float(cnt1[0] - cnt0[0]) / args.steps        # Philox blocks per launch
+        per_launch_s = (ms / args.steps) / 1e3 if world == 1 else (sum(ms_steps) / args.steps) / 1e3
+        sm_mhz = clk.get("sm_mhz") or sm_max
+        alu_peak = SMS * IMAD_PER_SM_PER_CLK * sm_max * 1e6 / PHILOX_IMAD / 1e9   # G blocks/s
+        achieved = draws / per_launch_s / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "rails": R, "sites": L, "time_steps_per_step": args.chunk,
+                       "site_updates_per_step": su_per_step, "fill": wl.fill,
+                       "electrodes": "injecting/extracting 1e9 Hz", "barriers": "per site N(0.40, 0.02) eV",
+                       "protocol": "triangle +-2 V, 1e5 steps/cycle", "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "one independent device per GPU" if world > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                         "unit": "G Philox4x32-10 blocks/s", "frac": achieved / alu_peak,
+                         "traffic": None,
+                         "peak_basis": "%d SMs x %d IMAD lanes/clk x %.0f MHz / %d IMAD ops per block" % (
+                             SMS, IMAD_PER_SM_PER_CLK, sm_max, PHILOX_IMAD),
+                         "hbm_basis": {"achieved_GBps": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9,
+                                       "peak_GBps": hbm, "peak_source": hbm_src,
+                                       "frac": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9 / hbm,
+                                       "bytes_per_site_update": BYTES_PER_SITE_UPDATE}},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                    "h2d_bytes_per_step": int(Vpin.nbytes),
+                    "d2h_bytes_per_step": int(Jpin.nbytes + Zpin.nbytes)},
+            "gpu_launches": args.steps,
+            "counters": {"philox_blocks_per_site_update": draws / su_per_step,
+                         "exact_fp64_decisions": int(cnt1[1] - cnt0[1]),
+                         "moves": int(cnt1[2] - cnt0[2])},
+            "wall_s": wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["kmc", "reference"], default="kmc")
+    ap.add_argument("--chunk", type=int, default=1000, help="time steps per benchmark step")
+    ap.add_argument("--rails", type=int, default=65536)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-steps", type=int, default=10, help="oracle time steps per reference step")
+    ap.add_argument("--ref-stride", type=int, default=16, help="oracle samples every n-th rail")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "kmc" and not os.environ.get("KMC_BENCH_ALLOW_FEW_WARMUP"):
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_kmc(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -66,12 +66,14 @@ struct kmc_handle {
     double *V = nullptr;
     int32_t *N0 = nullptr;
     double *P0site = nullptr;
+    float *P0f = nullptr;
     float2 *P0bnd = nullptr;
     DevConst *K = nullptr;
     unsigned long long *J = nullptr;
     unsigned long long *Zc = nullptr;
     kmc_log_entry *log = nullptr;
     unsigned long long *misc = nullptr;  // [0] log count, [1..3] counters, [4] scratch count
+    SweepArgs *args_dev = nullptr;       // device copy of args for the kernels' rare paths
     int64_t log_cap = 4096;
 
     SweepArgs args{};
@@ -174,14 +176,15 @@ int pick_launch(kmc_handle *h)
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (max_smem <= 0) max_smem = 48 * 1024;
     max_smem = std::min(max_smem, 200 * 1024);
-    while (warps > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush) >
-                            (size_t)max_smem)
+    const bool ps = h->P0site != nullptr;
+    while (warps > 1 &&
+           sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps) > (size_t)max_smem)
         warps >>= 1;
-    while (flush > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush) >
-                            (size_t)max_smem)
+    while (flush > 1 &&
+           sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps) > (size_t)max_smem)
         flush >>= 1;
     l.warps = warps;
-    l.smem = sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush);
+    l.smem = sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps);
     const int64_t rails_per_cta = (int64_t)G * warps;
     l.grid = (int)((p.n_rails + rails_per_cta - 1) / rails_per_cta);
     h->launch = l;
@@ -210,8 +213,10 @@ void fill_args(kmc_handle *h)
     a.V = h->V;
     a.N0 = h->N0;
     a.P0site = h->P0site;
+    a.P0f = h->P0f;
     a.P0bnd = h->P0bnd;
     a.K = h->K;
+    a.self = h->args_dev;
     a.J = h->J;
     a.Zc = h->Zc;
     a.log = h->log;
@@ -313,12 +318,15 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
                                            (size_t)Z);
     h->log = (kmc_log_entry *)h->alloc(sizeof(kmc_log_entry) * (size_t)h->log_cap);
     h->misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
-    if (!h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
+    h->args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
+    if (!h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
         return fail(KMC_E_NOMEM, "device allocation failed");
     if (Ea) {
         h->P0site = (double *)h->alloc(sizeof(double) * (size_t)(R * L));
+        h->P0f = (float *)h->alloc(sizeof(float) * (size_t)(R * L));
         h->P0bnd = (float2 *)h->alloc(sizeof(float2) * (size_t)(R * Z));
-        if (!h->P0site || !h->P0bnd) return fail(KMC_E_NOMEM, "device allocation failed (P0 table)");
+        if (!h->P0site || !h->P0f || !h->P0bnd)
+            return fail(KMC_E_NOMEM, "device allocation failed (P0 table)");
     }
     cudaStream_t s = h->stream;
     CK(cudaMemsetAsync(h->misc, 0, sizeof(unsigned long long) * 8, s), "memset");
@@ -352,6 +360,7 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
         CK(setup_p0_table(p, h->P0site, h->P0site, R * L, p0bad, s), "P0 table");
         CK(setup_p0_bounds(h->P0site, (int32_t)R, (int32_t)L, (int32_t)Z, h->K, h->P0bnd, s),
            "P0 bounds");
+        CK(setup_p0_float(h->P0site, R * L, h->P0f, s), "P0 float table");
     }
     // check derived values
     DevConst kc;
@@ -369,8 +378,13 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
         return fail(KMC_E_PROB, "per-site base probability outside [0, 1] (check Ea_site)");
     CK(cudaMemsetAsync(h->misc, 0, sizeof(unsigned long long) * 8, s), "memset");
     fill_args(h);
+    h->args.P0f_scalar = kc.P0f;
+    h->args.E_inf = kc.E_inf;
+    h->args.E_outf = kc.E_outf;
     rc = pick_launch(h);
     if (rc) return rc;
+    CK(cudaMemcpyAsync(h->args_dev, &h->args, sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
+       "copy args");
     CK(cudaStreamSynchronize(s), "create");
     return KMC_OK;
 }

@@ -43,8 +43,10 @@ struct SweepArgs {
     const double *V;           // [n_steps_total]
     const int32_t *N0;         // [R] background (initial) ion count per rail
     const double *P0site;      // [R][L] or null
+    const float *P0f;          // [R][L] P0site rounded to FP32, or null
     const float2 *P0bnd;       // [R][Z] (min, max) of P0site over the zone, or null
     const DevConst *K;
+    const SweepArgs *self;     // copy of these arguments in device memory (rare paths)
     unsigned long long *J;     // [n_steps_total] int64 two's complement
     unsigned long long *Zc;    // [n_steps_total][Z]
     kmc_log_entry *log;
@@ -58,6 +60,8 @@ struct SweepArgs {
     float inv_LkT;                // 1 / (L kT)
     float ka_f;                   // kappa alpha
     float delta;                  // relative half-width of the FP32 probability band
+    float P0f_scalar;             // scalar P0 in FP32 (host copy of DevConst::P0f)
+    float E_inf, E_outf;          // electrode base probabilities in FP32
 };
 
 // Launch configuration chosen on the host.
@@ -69,7 +73,7 @@ struct SweepLaunch {
     int grid;
 };
 
-size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush);
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite);
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
@@ -80,6 +84,7 @@ cudaError_t setup_p0_table(const kmc_params &p, const double *Ea, double *P0, in
                            cudaStream_t s);
 cudaError_t setup_p0_bounds(const double *P0, int32_t R, int32_t L, int32_t Z, const DevConst *K,
                             float2 *out, cudaStream_t s);
+cudaError_t setup_p0_float(const double *P0, int64_t n, float *out, cudaStream_t s);
 cudaError_t setup_row_counts(const uint8_t *occ, int64_t stride, int32_t R, int32_t L,
                              int32_t *N0, unsigned long long *bad, cudaStream_t s);
 cudaError_t setup_init_bernoulli(const kmc_params &p, uint8_t *occ, int64_t stride,

@@ -111,6 +111,13 @@ __global__ void p0_bounds_kernel(const double *P0, int32_t R, int32_t L, int32_t
     out[i] = make_float2(__double2float_rd(lo), __double2float_ru(hi));
 }
 
+__global__ void p0_float_kernel(const double *P0, int64_t n, float *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)P0[i];
+}
+
 // One warp per rail: ion count, and a count of bytes that are not 0 or 1.
 __global__ void row_counts_kernel(const uint8_t *occ, int64_t stride, int32_t R, int32_t L,
                                   int32_t *N0, unsigned long long *bad)
@@ -200,6 +207,12 @@ cudaError_t setup_p0_bounds(const double *P0, int32_t R, int32_t L, int32_t Z, c
 {
     const int64_t n = (int64_t)R * Z;
     p0_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P0, R, L, Z, K, out);
+    return cudaGetLastError();
+}
+
+cudaError_t setup_p0_float(const double *P0, int64_t n, float *out, cudaStream_t s)
+{
+    p0_float_kernel<<<grid_for(n, 256), 256, 0, s>>>(P0, n, out);
     return cudaGetLastError();
 }
 

@@ -18,8 +18,11 @@
 //    order and compares u <= p exactly.  Decisions are therefore identical to
 //    an all-FP64 evaluation.
 //  * Philox4x32-10 is evaluated only for sites whose decision can matter
-//    (occupied with a free neighbour, or an empty electrode site), after a
-//    warp-wide compaction so that all 32 lanes draw.
+//    (occupied with a free neighbour, or an electrode site), after a warp-wide
+//    compaction so that all 32 lanes draw.  The draw loop itself is lean: one
+//    Philox block, one zone-threshold load and two compares; hops are rare
+//    (p ~ 1e-4), so acceptance, electrodes and per-site refinement live on a
+//    rarely taken branch, and the exact FP64 path runs after the loop.
 //  * Moves are rare per step, so the move/conflict/apply phase runs only when
 //    the warp accepted at least one hop.
 //  * Per-step current and zone counts are reduced per CTA in shared memory and
@@ -35,6 +38,8 @@ namespace kmc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kDeferCap = 64;           // deferred (exact-path) candidates per warp and step
+constexpr uint16_t kNoSite = 0xFFFFu;   // empty electrode slot of an inactive rail
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
 // multiplies; the high halves are xor-ed with the other counter words and the
@@ -89,62 +94,77 @@ __device__ __forceinline__ uint32_t rej_thr(float p_hi)
     return __float2uint_ru(p_hi * 4294967296.0f);
 }
 
-struct WarpSmem {
-    uint4 *thr;     // [G][Z]  {acc R, rej R, acc L, rej L}
-    uint4 *thrE;    // [G][2]  electrode thresholds
-    float2 *zf;     // [G][Z]  FP32 (B, 1/(1+B))
-    int32_t *Pb;    // [G][Z+1] ions before each zone boundary
-    int32_t *Fs;    // [G] sum_z w_z (Pb_z + Pb_{z+1})
-    int32_t *inj;   // [2][G] injection flags (left electrode, right electrode)
-    uint32_t *mvR;  // [32 WPL] right-move sources
-    uint32_t *mvL;  // [32 WPL] left-move sources
-    uint32_t *list; // candidates
+// ---------------------------------------------------------------- shared memory
+// One warp's block: a fixed part whose offsets are compile-time constants and a
+// part that scales with G * Z (offsets from one runtime stride), so that the
+// kernel keeps only a base address and that stride in registers.
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int LPR, int WPL>
+struct Layout {
+    static constexpr int G = 32 / LPR;
+    static constexpr int W = 32 * WPL;                 // words per warp
+    static constexpr int LIST = 1024 * WPL + 2 * G;    // candidate slots
+    static constexpr size_t MVR = 0;
+    static constexpr size_t MVL = MVR + align16(4 * W);
+    static constexpr size_t FR = MVL + align16(4 * W);
+    static constexpr size_t FL = FR + align16(4 * W);
+    static constexpr size_t OW = FL + align16(4 * W);
+    static constexpr size_t THRE = OW + align16(4 * W);        // uint4 [G][2]
+    static constexpr size_t INJ = THRE + align16(16 * 2 * G);  // int [2][G]
+    static constexpr size_t N0S = INJ + align16(4 * 2 * G);    // int [G]
+    static constexpr size_t FS = N0S + align16(4 * G);         // int [G]
+    static constexpr size_t NDEF = FS + align16(4 * G);        // int [4]
+    static constexpr size_t DEF = NDEF + 16;                   // uint16 [kDeferCap]
+    static constexpr size_t LST = DEF + align16(2 * 64);       // uint16 [LIST]
+    static constexpr size_t FIXED = LST + align16(2 * LIST);
+    // variable part: rm uint2 [G Z + 2 G] (zones, then the two electrode sites of
+    // each rail), zf and P0b float2 [G][Z] (gz8 = align16(8 G Z) bytes each),
+    // Pb int [G][Z+1], then P0f float [G][32 LPR WPL] (per-site mode only)
+    __host__ __device__ static size_t rm_bytes(int Z) { return align16((size_t)8 * G * (Z + 2)); }
+    __host__ __device__ static size_t gz8(int Z) { return align16((size_t)8 * G * Z); }
+    __host__ __device__ static size_t pb_bytes(int Z) { return align16((size_t)4 * G * (Z + 1)); }
+    __host__ __device__ static size_t bytes(int Z, bool persite)
+    {
+        return FIXED + rm_bytes(Z) + 2 * gz8(Z) + pb_bytes(Z) +
+               (persite ? align16((size_t)4 * 1024 * WPL) : 0);
+    }
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+template <int LPR, int WPL>
+struct WarpSmem {
+    using Ly = Layout<LPR, WPL>;
+    uint8_t *b;     // block base (shared memory)
+    uint32_t rz;    // Layout::rm_bytes(Z)
+    uint32_t gz;    // Layout::gz8(Z)
+    uint32_t pbz;   // Layout::pb_bytes(Z)
+    __device__ uint32_t *mvR() const { return (uint32_t *)(b + Ly::MVR); }
+    __device__ uint32_t *mvL() const { return (uint32_t *)(b + Ly::MVL); }
+    __device__ uint32_t *fR() const { return (uint32_t *)(b + Ly::FR); }
+    __device__ uint32_t *fL() const { return (uint32_t *)(b + Ly::FL); }
+    __device__ uint32_t *ow() const { return (uint32_t *)(b + Ly::OW); }
+    __device__ uint4 *thrE() const { return (uint4 *)(b + Ly::THRE); }
+    __device__ int32_t *inj() const { return (int32_t *)(b + Ly::INJ); }
+    __device__ int32_t *N0s() const { return (int32_t *)(b + Ly::N0S); }
+    __device__ int32_t *Fs() const { return (int32_t *)(b + Ly::FS); }
+    __device__ int32_t *ndef() const { return (int32_t *)(b + Ly::NDEF); }
+    // window mid voltage (FP32), stored next to the deferral counter
+    __device__ float &vmid_ref() const { return *(float *)(b + Ly::NDEF + 4); }
+    __device__ uint16_t *def() const { return (uint16_t *)(b + Ly::DEF); }
+    __device__ uint16_t *list() const { return (uint16_t *)(b + Ly::LST); }
+    __device__ uint2 *rm() const { return (uint2 *)(b + Ly::FIXED); }
+    __device__ float2 *zf() const { return (float2 *)(b + Ly::FIXED + rz); }
+    __device__ float2 *P0b() const { return (float2 *)(b + Ly::FIXED + rz + gz); }
+    __device__ int32_t *Pb() const { return (int32_t *)(b + Ly::FIXED + rz + 2 * gz); }
+    __device__ float *P0f() const { return (float *)(b + Ly::FIXED + rz + 2 * gz + pbz); }
+};
 
-__host__ __device__ inline size_t warp_block_bytes(int G, int Z, int wpl)
-{
-    size_t b = 0;
-    b += align16(sizeof(uint4) * G * Z);
-    b += align16(sizeof(uint4) * G * 2);
-    b += align16(sizeof(float2) * G * Z);
-    b += align16(sizeof(int32_t) * G * (Z + 1));
-    b += align16(sizeof(int32_t) * G);
-    b += align16(sizeof(int32_t) * 2 * G);
-    b += align16(sizeof(uint32_t) * 2 * 32 * wpl);
-    b += align16(sizeof(uint32_t) * (1024 * wpl + 2 * G));
-    return b;
-}
-
-__device__ inline WarpSmem carve(uint8_t *base, int G, int Z, int wpl)
-{
-    WarpSmem w;
-    size_t o = 0;
-    w.thr = (uint4 *)(base + o);
-    o += align16(sizeof(uint4) * G * Z);
-    w.thrE = (uint4 *)(base + o);
-    o += align16(sizeof(uint4) * G * 2);
-    w.zf = (float2 *)(base + o);
-    o += align16(sizeof(float2) * G * Z);
-    w.Pb = (int32_t *)(base + o);
-    o += align16(sizeof(int32_t) * G * (Z + 1));
-    w.Fs = (int32_t *)(base + o);
-    o += align16(sizeof(int32_t) * G);
-    w.inj = (int32_t *)(base + o);
-    o += align16(sizeof(int32_t) * 2 * G);
-    w.mvR = (uint32_t *)(base + o);
-    w.mvL = w.mvR + 32 * wpl;
-    o += align16(sizeof(uint32_t) * 2 * 32 * wpl);
-    w.list = (uint32_t *)(base + o);
-    return w;
-}
-
+// --------------------------------------------------------- exact FP64 path
 // Exact FP64 zone quantities (B_z, 1/(1+B_z)) for zone zt of one rail, with
 // the operation order of the oracle: excess C_z, enclosed charge Q_z, mean
 // Qbar, dV_z (S2.1.8), dE_z (Eq. 3), B_z (Eq. 4).  Every operation is an
 // explicitly rounded intrinsic so that no contraction changes the result.
-__device__ __noinline__ void exact_zone(const int32_t *Pb, const DevConst *Kp, int Z, int L,
+__device__ __forceinline__ void exact_zone(const int32_t *Pb, const DevConst *Kp, int Z, int L,
                                         int32_t n0, double V, int zt, double *B, double *inv)
 {
     const DevConst &K = *Kp;
@@ -168,7 +188,7 @@ __device__ __noinline__ void exact_zone(const int32_t *Pb, const DevConst *Kp, i
 }
 
 // Exact decision u <= p for the 64-bit word w, with near-threshold logging.
-__device__ __noinline__ bool exact_trial(uint64_t w, double p, kmc_log_entry *log,
+__device__ __forceinline__ bool exact_trial(uint64_t w, double p, kmc_log_entry *log,
                                          unsigned long long *log_count, int64_t log_cap,
                                          int32_t rail, uint32_t step, int32_t site, int32_t dir,
                                          int32_t kind)
@@ -192,10 +212,153 @@ __device__ __noinline__ bool exact_trial(uint64_t w, double p, kmc_log_entry *lo
     return u <= p;
 }
 
+// ------------------------------------------------------------ one decision
+// Bounded decision of one candidate from the step-start state kept in shared
+// memory: dR, dL in {0 reject (or direction blocked), 1 accept, 2 undecided},
+// the move kinds (0 inner hop, 1 injection, 2 extraction), and where to record
+// the move.  Thresholds come from the zone's FP32 (B, 1/(1+B)) and the band
+// factors (flo, fhi); electrode and per-site base probabilities are applied here.
+struct Decision {
+    int dR, dL, kindR, kindL;
+    bool occd;
+    int idx;
+    uint32_t bit;
+};
+
+// Band factors: p_lo = p flo, p_hi = p fhi bracket the exact p.
+__device__ __forceinline__ int bounded(uint32_t h, float p, float flo, float fhi)
+{
+    return h < acc_thr(p * flo) ? 1 : (h > rej_thr(p * fhi) ? 0 : 2);
+}
+
 template <int LPR, int WPL>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
+__device__ __forceinline__ Decision decide(const WarpSmem<LPR, WPL> &S, const SweepArgs *g,
+                                           uint4 x, int site, int g2, int z, bool isE,
+                                           bool persite, float flo, float fhi)
+{
+    const int L = g->L, Z = g->Z;
+    Decision D;
+    D.idx = g2 * LPR * WPL + (site >> 5);
+    D.bit = 1u << (site & 31);
+    D.occd = (S.ow()[D.idx] & D.bit) != 0;
+    const bool tryR = D.occd ? (S.fR()[D.idx] & D.bit) != 0 : (isE && site == 0);
+    const bool tryL = D.occd ? (S.fL()[D.idx] & D.bit) != 0 : (isE && site == L - 1);
+    const float2 bi = S.zf()[g2 * Z + z];          // (B, 1/(1+B)); (0, 0) when undecidable
+    const bool ok = bi.y > 0.0f;
+    const float sR = bi.y * bi.x, sL = bi.y;
+    D.kindR = 0;
+    D.kindL = 0;
+    // base probability of each trial: P0 (scalar or this site's), or electrode exchange
+    float bR = persite ? S.P0f()[g2 * (32 * LPR * WPL) + site] : g->K->P0f;
+    float bL = bR;
+    if (isE) {
+        if (!D.occd) {              // injection: site 0 via the right draw, L-1 via the left
+            if (site == 0) {
+                bR = g->K->E_inf;
+                D.kindR = 1;
+            } else {
+                bL = g->K->E_inf;
+                D.kindL = 1;
+            }
+        } else {                    // extraction through the adjacent electrode
+            if (site == 0) {
+                bL = g->K->E_outf;
+                D.kindL = 2;
+            }
+            if (site == L - 1) {
+                bR = g->K->E_outf;
+                D.kindR = 2;
+            }
+        }
+    }
+    D.dR = tryR ? (ok ? bounded(x.y, bR * sR, flo, fhi) : 2) : 0;
+    D.dL = tryL ? (ok ? bounded(x.w, bL * sL, flo, fhi) : 2) : 0;
+    return D;
+}
+
+// Record an accepted net move (both trials accepted: the ion stays, S2.1.7).
+template <int LPR, int WPL>
+__device__ __forceinline__ bool record_move(const WarpSmem<LPR, WPL> &S, const Decision &D, int g2)
 {
     constexpr int G = 32 / LPR;
+    if (D.dR == 1 && D.dL != 1) {
+        if (!D.occd) S.inj()[g2] = 1;               // injection into site 0
+        else atomicOr(&S.mvR()[D.idx], D.bit);
+        return true;
+    }
+    if (D.dL == 1 && D.dR != 1) {
+        if (!D.occd) S.inj()[G + g2] = 1;           // injection into site L-1
+        else atomicOr(&S.mvL()[D.idx], D.bit);
+        return true;
+    }
+    return false;
+}
+
+// Slow path of one candidate (taken for roughly one draw in a thousand):
+// recomputes the draw, decides against the FP32 band and records the move.
+// With exact == false an undecided candidate is queued for the exact pass;
+// with exact == true only undecided candidates are handled, by recomputing p
+// in FP64 with the oracle's operation order (exact_zone) and comparing u <= p.
+// Reads the launch arguments through their copy in global memory (g), which
+// keeps the parameter block in the constant bank for the draw loop.
+template <int LPR, int WPL>
+__device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const SweepArgs *g, int i,
+                                            int n_inner, int64_t rail0, uint32_t t,
+                                            const uint8_t *zone_tab, bool persite, float flo,
+                                            float fhi, bool exact, uint32_t xy, uint32_t xw)
+{
+    const uint16_t dsc = S.list()[i];
+    const int site = dsc & 0x7FF, g2 = dsc >> 11;
+    const uint32_t r2 = (uint32_t)(rail0 + g2);
+    // the bounded decision needs only the high words (x1, x3) of the draw; the
+    // exact pass recomputes the whole block
+    const uint4 x = exact ? philox((uint32_t)site, r2, t, g->instance, g->rk0, g->rk1)
+                          : make_uint4(0u, xy, 0u, xw);
+    const int z = zone_tab[site];
+    const bool isE = i >= n_inner;
+    Decision D = decide<LPR, WPL>(S, g, x, site, g2, z, isE, persite, flo, fhi);
+    const bool undecided = D.dR == 2 || D.dL == 2;
+    if (!exact) {
+        if (undecided) {
+            const int slot = atomicAdd(S.ndef(), 1);
+            if (slot < kDeferCap) S.def()[slot] = (uint16_t)i;
+            return false;
+        }
+        return record_move<LPR, WPL>(S, D, g2);
+    }
+    if (!undecided) return false;   // decided (and applied) in the draw loop
+    const DevConst *K = g->K;
+    const int L = g->L, Z = g->Z;
+    double B, inv;
+    exact_zone(S.Pb() + g2 * (Z + 1), K, Z, L, S.N0s()[g2], g->V[t], z, &B, &inv);
+    const double P0k = persite ? g->P0site[(int64_t)r2 * L + site] : K->P0;
+    unsigned ne = 0;
+    if (D.dR == 2) {
+        const double base = D.kindR == 1 ? K->E_in : (D.kindR == 2 ? K->E_out : P0k);
+        const double p = __dmul_rn(__dmul_rn(base, inv), B);       // Eq. 6
+        D.dR = exact_trial(((uint64_t)x.y << 32) | x.x, p, g->log, g->log_count, g->log_cap,
+                           (int32_t)r2, t, site, 0, D.kindR) ? 1 : 0;
+        ++ne;
+    }
+    if (D.dL == 2) {
+        const double base = D.kindL == 1 ? K->E_in : (D.kindL == 2 ? K->E_out : P0k);
+        const double p = __dmul_rn(base, inv);                      // Eq. 5
+        D.dL = exact_trial(((uint64_t)x.w << 32) | x.z, p, g->log, g->log_count, g->log_cap,
+                           (int32_t)r2, t, site, 1, D.kindL) ? 1 : 0;
+        ++ne;
+    }
+    atomicAdd(&g->counters[1], (unsigned long long)ne);
+    return record_move<LPR, WPL>(S, D, g2);
+}
+
+template <int LPR, int WPL>
+// 80 registers (3 CTAs of 256 threads per SM): the draw loop fits; the exact
+// FP64 path, which runs for about one draw in a million, may spill.
+__global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
+{
+    constexpr int G = 32 / LPR;
+    constexpr int LSEG = 32 * LPR * WPL;  // site capacity of one rail slot
+    constexpr int VWIN = 32;              // steps per voltage window of the FP32 bounds
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -205,24 +368,46 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
     const int wbase = sl * WPL;
     const int L = a.L, Z = a.Z;
     const bool open = a.electrodes == 1;
+    const bool persite = a.P0bnd != nullptr;
     const int64_t rail0 = ((int64_t)blockIdx.x * nwarps + warp) * G;
     const int64_t rail = rail0 + seg;
     const bool active = rail < a.R;
+    const int nact = (int)max((int64_t)0, min((int64_t)G, (int64_t)a.R - rail0));
 
-    const size_t wb = warp_block_bytes(G, Z, WPL);
-    WarpSmem S = carve(smem + (size_t)warp * wb, G, Z, WPL);
+    using Ly = Layout<LPR, WPL>;
+    const size_t wb = Ly::bytes(Z, persite);
+    WarpSmem<LPR, WPL> S;
+    S.b = smem + (size_t)warp * wb;
+    S.rz = (uint32_t)Ly::rm_bytes(Z);
+    S.gz = (uint32_t)Ly::gz8(Z);
+    S.pbz = (uint32_t)Ly::pb_bytes(Z);
     int32_t *trace = (int32_t *)(smem + (size_t)nwarps * wb);
     uint8_t *zone_tab = (uint8_t *)(trace + (size_t)a.flush * (1 + Z));
 
-    // ---- per-CTA tables
+    // ---- per-CTA tables and per-warp staging
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         int z = 0;
         while (a.bnd[z + 1] <= k) ++z;
         zone_tab[k] = (uint8_t)z;
     }
     for (int i = threadIdx.x; i < a.flush * (1 + Z); i += blockDim.x) trace[i] = 0;
-    for (int i = lane; i < 2 * 32 * WPL; i += 32) S.mvR[i] = 0;
-    for (int i = lane; i < 2 * G; i += 32) S.inj[i] = 0;
+    for (int i = lane; i < 32 * WPL; i += 32) {
+        S.mvR()[i] = 0;
+        S.mvL()[i] = 0;
+    }
+    for (int i = lane; i < 2 * G; i += 32) S.inj()[i] = 0;
+    if (sl == 0) S.N0s()[seg] = active ? a.N0[rail] : 0;
+    if (persite) {
+        for (int pi = lane; pi < G * Z; pi += 32) {
+            const int64_t r2 = rail0 + pi / Z;
+            S.P0b()[pi] = r2 < a.R ? a.P0bnd[r2 * Z + pi % Z] : make_float2(0.0f, 0.0f);
+        }
+        for (int q = lane; q < G * L; q += 32) {
+            const int g2 = q / L, k = q - g2 * L;
+            const int64_t r2 = rail0 + g2;
+            S.P0f()[g2 * LSEG + k] = r2 < a.R ? a.P0f[r2 * L + k] : 0.0f;
+        }
+    }
 
     // ---- per-lane site masks and owned zone boundaries
     uint32_t vm[WPL], firstm[WPL], lastm[WPL], o[WPL];
@@ -255,266 +440,261 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             }
         }
     }
-    const int32_t n0_seg = active ? a.N0[rail] : 0;
-    const float delta = a.delta;
-    const DevConst *K = a.K;
-    const float P0f = K->P0f, E_inf = K->E_inf, E_outf = K->E_outf;
-    unsigned long long n_draw = 0, n_exact = 0, n_move = 0;
+    bool dirty = true;      // occupancy changed since the candidate list was built
+    int win_end = 0;        // first step after the current voltage window
+    // band factors: p_lo = p flo <= p <= p fhi = p_hi for every step of the window
+    float flo = 1.0f - a.delta, fhi = 1.0f + a.delta;
+    int n_inner = 0, nlist = 0;
+    unsigned n_draw = 0, n_move = 0;
     __syncthreads();
 
     for (int c0 = 0; c0 < a.n_steps; c0 += a.flush) {
         const int c1 = min(a.n_steps, c0 + a.flush);
         for (int s = c0; s < c1; ++s) {
             const uint32_t t = (uint32_t)(a.t0 + s);
-            const double Vd = a.V[t];
-            const float Vf = (float)Vd;
             int32_t *tr = trace + (s - c0) * (1 + Z);
 
-            // ---- 1. zone counts: segmented scan of popcounts
-            int cnt = 0;
+            if (dirty) {
+                // ---- 1. zone counts: segmented scan of popcounts
+                int cnt = 0;
 #pragma unroll
-            for (int j = 0; j < WPL; ++j) cnt += __popc(o[j]);
-            int incl = cnt;
+                for (int j = 0; j < WPL; ++j) cnt += __popc(o[j]);
+                int incl = cnt;
 #pragma unroll
-            for (int off = 1; off < LPR; off <<= 1) {
-                const int v = __shfl_up_sync(FULL, incl, off, LPR);
-                if (sl >= off) incl += v;
-            }
-            const int excl = incl - cnt;
-            const int total = __shfl_sync(FULL, incl, LPR - 1, LPR);
-            int fpart = 0;
-            for (int z = zlo; z <= zhi; ++z) {
-                const int b = a.bnd[z];
-                const int j = (b >> 5) - wbase;
-                const uint32_t below = (1u << (b & 31)) - 1u;
-                int P = excl;
-                if (WPL == 2) {
-                    if (j == 1) P += __popc(o[0]) + __popc(o[WPL - 1] & below);
-                    else P += __popc(o[0] & below);
-                } else {
-                    P += __popc(o[0] & below);
+                for (int off2 = 1; off2 < LPR; off2 <<= 1) {
+                    const int v = __shfl_up_sync(FULL, incl, off2, LPR);
+                    if (sl >= off2) incl += v;
                 }
-                S.Pb[seg * (Z + 1) + z] = P;
-                fpart += P * a.wsum[z];
-            }
-            if (sl == 0) S.Pb[seg * (Z + 1)] = 0;
-            if (sl == LPR - 1) {
-                S.Pb[seg * (Z + 1) + Z] = total;
-                fpart += total * a.wsum[Z];
-            }
+                const int excl = incl - cnt;
+                const int total = __shfl_sync(FULL, incl, LPR - 1, LPR);
+                int fpart = 0;
+                for (int z = zlo; z <= zhi; ++z) {
+                    const int b = a.bnd[z];
+                    const int j = (b >> 5) - wbase;
+                    const uint32_t below = (1u << (b & 31)) - 1u;
+                    int P = excl;
+                    if (WPL == 2) {
+                        if (j == 1) P += __popc(o[0]) + __popc(o[WPL - 1] & below);
+                        else P += __popc(o[0] & below);
+                    } else {
+                        P += __popc(o[0] & below);
+                    }
+                    S.Pb()[seg * (Z + 1) + z] = P;
+                    fpart += P * a.wsum[z];
+                }
+                if (sl == 0) S.Pb()[seg * (Z + 1)] = 0;
+                if (sl == LPR - 1) {
+                    S.Pb()[seg * (Z + 1) + Z] = total;
+                    fpart += total * a.wsum[Z];
+                }
 #pragma unroll
-            for (int off = LPR / 2; off >= 1; off >>= 1) fpart += __shfl_xor_sync(FULL, fpart, off, LPR);
-            if (sl == 0) S.Fs[seg] = fpart;
-            __syncwarp();
+                for (int off2 = LPR / 2; off2 >= 1; off2 >>= 1)
+                    fpart += __shfl_xor_sync(FULL, fpart, off2, LPR);
+                if (sl == 0) S.Fs()[seg] = fpart;
 
-            // ---- 2. field and FP32 decision intervals per (rail, zone)
+                // ---- 3. candidates: occupied sites with a free neighbour; the two
+                //         electrode sites of an open rail are listed separately
+                uint32_t cand[WPL];
+                {
+                    uint32_t f[WPL];
+#pragma unroll
+                    for (int j = 0; j < WPL; ++j) f[j] = ~o[j] & vm[j];
+                    const uint32_t f_prev = __shfl_up_sync(FULL, f[WPL - 1], 1, LPR);
+                    const uint32_t f_next = __shfl_down_sync(FULL, f[0], 1, LPR);
+#pragma unroll
+                    for (int j = 0; j < WPL; ++j) {
+                        const uint32_t cp = j > 0 ? (f[j > 0 ? j - 1 : 0] >> 31)
+                                                  : (sl > 0 ? (f_prev >> 31) : (open ? 1u : 0u));
+                        const uint32_t cn = j < WPL - 1 ? (f[j < WPL - 1 ? j + 1 : 0] & 1u)
+                                                        : (sl < LPR - 1 ? (f_next & 1u) : 0u);
+                        const uint32_t fL = (f[j] << 1) | cp;
+                        uint32_t fR = (f[j] >> 1) | (cn << 31);
+                        if (open) fR |= lastm[j];
+                        const int wi = seg * LPR * WPL + wbase + j;
+                        S.fR()[wi] = fR;
+                        S.fL()[wi] = fL;
+                        S.ow()[wi] = o[j];
+                        uint32_t c = o[j] & (fL | fR);
+                        if (open) c &= ~(firstm[j] | lastm[j]);
+                        cand[j] = active ? c : 0u;
+                    }
+                }
+
+                // ---- 4. warp-wide compaction of candidates
+                int nc = 0;
+#pragma unroll
+                for (int j = 0; j < WPL; ++j) nc += __popc(cand[j]);
+                int ic = nc;
+#pragma unroll
+                for (int off2 = 1; off2 < 32; off2 <<= 1) {
+                    const int v = __shfl_up_sync(FULL, ic, off2);
+                    if (lane >= off2) ic += v;
+                }
+                int pos = ic - nc;
+                n_inner = __shfl_sync(FULL, ic, 31);
+#pragma unroll
+                for (int j = 0; j < WPL; ++j) {
+                    uint32_t m = cand[j];
+                    const uint32_t base = (uint32_t)(32 * (wbase + j)) | ((uint32_t)seg << 11);
+                    while (m) {
+                        S.list()[pos++] = (uint16_t)(base + (uint32_t)(__ffs(m) - 1));
+                        m &= m - 1;
+                    }
+                }
+                if (open && seg < nact) {
+                    const uint16_t tag = (uint16_t)(seg << 11);
+                    if (sl == 0) S.list()[n_inner + 2 * seg] = tag;
+#pragma unroll
+                    for (int j = 0; j < WPL; ++j)
+                        if (lastm[j]) S.list()[n_inner + 2 * seg + 1] = (uint16_t)(tag | (L - 1));
+                }
+                nlist = n_inner + (open ? 2 * nact : 0);
+                __syncwarp();
+            }
+
+            // ---- 2. field and FP32 decision bands per (rail, zone), valid for
+            //         every step of the voltage window while the occupancy holds
+            if (dirty || s >= win_end) {
+                if (s >= win_end) {
+                    win_end = min(s + VWIN, a.n_steps);
+                    const int k = min(lane, win_end - 1 - s);
+                    const double v = a.V[t + k];
+                    float vlo = __double2float_rd(v), vhi = __double2float_ru(v);
+#pragma unroll
+                    for (int off2 = 16; off2 >= 1; off2 >>= 1) {
+                        vlo = fminf(vlo, __shfl_xor_sync(FULL, vlo, off2));
+                        vhi = fmaxf(vhi, __shfl_xor_sync(FULL, vhi, off2));
+                    }
+                    // Evaluating at the window's mid voltage moves the exponent x of
+                    // Eq. 4 by at most h = (vhi - vlo) / (2 L kT); B/(1+B) and 1/(1+B)
+                    // have logarithmic derivatives in [-1, 1] with respect to x, so
+                    // both change by a factor within [e^-h, e^h].  FP32 evaluation
+                    // errors (about 1e-5 relative for |x| <= 40) are covered by delta.
+                    const float h = 0.5f * (vhi - vlo) * a.inv_LkT;
+                    const float eh = __expf(h) * (1.0f + 1.0f / 65536.0f);
+                    fhi = (1.0f + a.delta) * eh;
+                    flo = (1.0f - a.delta) / eh;
+                    S.vmid_ref() = 0.5f * (vlo + vhi);
+                }
+                const float Vf = S.vmid_ref();
+                for (int pi = lane; pi < G * Z; pi += 32) {
+                    const int g2 = pi / Z;
+                    const int z = pi - g2 * Z;
+                    float2 zf = make_float2(0.0f, 0.0f);
+                    uint2 rm = make_uint2(FULL, FULL);
+                    if (g2 < nact) {
+                        const int Pz = S.Pb()[g2 * (Z + 1) + z];
+                        const int Pz1 = S.Pb()[g2 * (Z + 1) + z + 1];
+                        const float qd = 0.5f * ((float)(Pz + Pz1) - (float)S.Fs()[g2] * a.inv_L) -
+                                         (float)S.N0s()[g2] * a.cz[z];
+                        const float dV = Vf - a.ka_f * qd;
+                        const float x = -dV * a.inv_LkT;
+                        if (fabsf(x) <= 40.0f) {
+                            const float B = __expf(x);
+                            const float inv = __fdividef(1.0f, 1.0f + B);
+                            float bhi = a.P0f_scalar;
+                            if (persite) bhi = S.P0b()[pi].y;
+                            rm = make_uint2(rej_thr(bhi * inv * B * fhi), rej_thr(bhi * inv * fhi));
+                            zf = make_float2(B, inv);
+                        }
+                    }
+                    // rm: reject-sure bounds for inner hops; (FULL, FULL) sends every
+                    // draw of the zone to the slow path (zf == 0 marks it undecidable)
+                    S.rm()[pi] = rm;
+                    S.zf()[pi] = zf;
+                    if (open && g2 < nact && (z == 0 || z == Z - 1)) {
+                        // reject-sure bounds of the electrode sites: an occupied site 0
+                        // can hop right (inner) or leave left (extraction); an empty one
+                        // can only receive an injection through its right draw.  Site
+                        // L-1 mirrors this.  A bound of 0 marks a direction never tried.
+                        const float sR = zf.y * zf.x, sL = zf.y;
+                        const bool ok = zf.y > 0.0f;
+                        const float bhi = persite ? S.P0b()[pi].y : a.P0f_scalar;
+                        const float Ein = a.E_inf, Eout = a.E_outf;
+                        if (z == 0) {
+                            const bool occ0 = (S.ow()[g2 * LPR * WPL] & 1u) != 0;
+                            uint2 e = occ0 ? make_uint2(rej_thr(bhi * sR * fhi), rej_thr(Eout * sL * fhi))
+                                           : make_uint2(rej_thr(Ein * sR * fhi), 0u);
+                            S.rm()[G * Z + 2 * g2] = ok ? e : make_uint2(FULL, FULL);
+                        }
+                        if (z == Z - 1) {
+                            const int wl = g2 * LPR * WPL + ((L - 1) >> 5);
+                            const bool occl = (S.ow()[wl] >> ((L - 1) & 31)) & 1u;
+                            uint2 e = occl ? make_uint2(rej_thr(Eout * sR * fhi), rej_thr(bhi * sL * fhi))
+                                           : make_uint2(0u, rej_thr(Ein * sL * fhi));
+                            S.rm()[G * Z + 2 * g2 + 1] = ok ? e : make_uint2(FULL, FULL);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+
+            // ---- zone counts of the step-start occupancy into the trace
             for (int pi = lane; pi < G * Z; pi += 32) {
                 const int g2 = pi / Z;
                 const int z = pi - g2 * Z;
-                const int64_t r2 = rail0 + g2;
-                const int Pz = S.Pb[g2 * (Z + 1) + z];
-                const int Pz1 = S.Pb[g2 * (Z + 1) + z + 1];
-                if (Pz1 != Pz) atomicAdd(&tr[1 + z], Pz1 - Pz);
-                if (r2 >= a.R) continue;
-                const int32_t n0 = a.N0[r2];
-                const float qd = 0.5f * ((float)(Pz + Pz1) - (float)S.Fs[g2] * a.inv_L) -
-                                 (float)n0 * a.cz[z];
-                const float dV = Vf - a.ka_f * qd;
-                const float x = -dV * a.inv_LkT;
-                uint4 th;
-                if (!(fabsf(x) <= 40.0f)) {
-                    th = make_uint4(0u, FULL, 0u, FULL);  // undecidable in FP32: exact path
-                    S.zf[pi] = make_float2(0.0f, 0.0f);
-                    if (open && z == 0) S.thrE[g2 * 2 + 0] = th;
-                    if (open && z == Z - 1) S.thrE[g2 * 2 + 1] = th;
-                } else {
-                    const float B = expf(x);
-                    const float inv = 1.0f / (1.0f + B);
-                    const float lo = 1.0f - delta, hi = 1.0f + delta;
-                    float blo = P0f, bhi = P0f;
-                    if (a.P0bnd) {
-                        const float2 pb = a.P0bnd[r2 * Z + z];
-                        blo = pb.x;
-                        bhi = pb.y;
-                    }
-                    const float sR = inv * B, sL = inv;
-                    th = make_uint4(acc_thr(blo * sR * lo), rej_thr(bhi * sR * hi),
-                                    acc_thr(blo * sL * lo), rej_thr(bhi * sL * hi));
-                    S.zf[pi] = make_float2(B, inv);
-                    if (open && z == 0)  // injection into site 0 (right), extraction from 0 (left)
-                        S.thrE[g2 * 2 + 0] =
-                            make_uint4(acc_thr(E_inf * sR * lo), rej_thr(E_inf * sR * hi),
-                                       acc_thr(E_outf * sL * lo), rej_thr(E_outf * sL * hi));
-                    if (open && z == Z - 1)  // extraction from L-1 (right), injection into L-1 (left)
-                        S.thrE[g2 * 2 + 1] =
-                            make_uint4(acc_thr(E_outf * sR * lo), rej_thr(E_outf * sR * hi),
-                                       acc_thr(E_inf * sL * lo), rej_thr(E_inf * sL * hi));
-                }
-                S.thr[pi] = th;
+                const int nz = S.Pb()[g2 * (Z + 1) + z + 1] - S.Pb()[g2 * (Z + 1) + z];
+                if (nz != 0) atomicAdd(&tr[1 + z], nz);
+            }
+            if (lane == 0) {
+                S.ndef()[0] = 0;
+                n_draw += (unsigned)nlist;
             }
             __syncwarp();
 
-            // ---- 3. candidates: occupied with a free neighbour, empty electrode sites
-            uint32_t fL[WPL], fR[WPL], cand[WPL];
-            {
-                uint32_t f[WPL];
-#pragma unroll
-                for (int j = 0; j < WPL; ++j) f[j] = ~o[j] & vm[j];
-                const uint32_t f_prev = __shfl_up_sync(FULL, f[WPL - 1], 1, LPR);
-                const uint32_t f_next = __shfl_down_sync(FULL, f[0], 1, LPR);
-#pragma unroll
-                for (int j = 0; j < WPL; ++j) {
-                    const uint32_t cp = j > 0 ? (f[j > 0 ? j - 1 : 0] >> 31)
-                                              : (sl > 0 ? (f_prev >> 31) : (open ? 1u : 0u));
-                    const uint32_t cn = j < WPL - 1 ? (f[j < WPL - 1 ? j + 1 : 0] & 1u)
-                                                    : (sl < LPR - 1 ? (f_next & 1u) : 0u);
-                    fL[j] = (f[j] << 1) | cp;
-                    fR[j] = (f[j] >> 1) | (cn << 31);
-                    if (open) fR[j] |= lastm[j];
-                    const uint32_t inj = open ? ((firstm[j] | lastm[j]) & ~o[j]) : 0u;
-                    cand[j] = active ? ((o[j] & (fL[j] | fR[j])) | inj) : 0u;
-                }
-            }
-
-            // ---- 4. warp-wide compaction of candidates
-            int nc = 0;
-#pragma unroll
-            for (int j = 0; j < WPL; ++j) nc += __popc(cand[j]);
-            int ic = nc;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int v = __shfl_up_sync(FULL, ic, off);
-                if (lane >= off) ic += v;
-            }
-            int pos = ic - nc;
-            const int ntot = __shfl_sync(FULL, ic, 31);
-#pragma unroll
-            for (int j = 0; j < WPL; ++j) {
-                uint32_t m = cand[j];
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    const uint32_t bit = 1u << b;
-                    const bool occd = (o[j] & bit) != 0;
-                    const bool tR = occd ? (fR[j] & bit) != 0 : (firstm[j] & bit) != 0;
-                    const bool tL = occd ? (fL[j] & bit) != 0 : (lastm[j] & bit) != 0;
-                    S.list[pos++] = (uint32_t)(32 * (wbase + j) + b) | ((uint32_t)seg << 11) |
-                                    (tR ? (1u << 16) : 0u) | (tL ? (1u << 17) : 0u) |
-                                    (occd ? 0u : (1u << 18));
-                }
-            }
-            __syncwarp();
-            if (lane == 0) n_draw += (unsigned long long)ntot;
-
-            // ---- 5. draws and decisions
+            // ---- 5. draws: two Philox blocks per lane per iteration; everything
+            //         but the reject-sure test is on the slow path
             bool moved = false;
-            for (int i = lane; i < ntot; i += 32) {
-                const uint32_t dsc = S.list[i];
-                const int site = (int)(dsc & 0x7FFu);
-                const int g2 = (int)((dsc >> 11) & 31u);
-                const bool tryR = (dsc >> 16) & 1u, tryL = (dsc >> 17) & 1u;
-                const bool empty = (dsc >> 18) & 1u;
-                const uint32_t r2 = (uint32_t)(rail0 + g2);
-                const uint4 x = philox((uint32_t)site, r2, t, a.instance, a.rk0, a.rk1);
-                const int z = zone_tab[site];
-                const uint4 th = S.thr[g2 * Z + z];
-                uint32_t aR = th.x, rR = th.y, aL = th.z, rL = th.w;
-                int kindR = 0, kindL = 0;
-                bool siteP0 = a.P0bnd != nullptr;  // per-site base probability applies
-                bool siteP0R = siteP0, siteP0L = siteP0;
-                if (open) {
-                    if (empty) {
-                        if (site == 0) {
-                            const uint4 e = S.thrE[g2 * 2 + 0];
-                            aR = e.x;
-                            rR = e.y;
-                            kindR = 1;
-                        } else {
-                            const uint4 e = S.thrE[g2 * 2 + 1];
-                            aL = e.z;
-                            rL = e.w;
-                            kindL = 1;
-                        }
-                        siteP0R = siteP0L = false;
-                    } else {
-                        if (site == 0) {
-                            const uint4 e = S.thrE[g2 * 2 + 0];
-                            aL = e.z;
-                            rL = e.w;
-                            kindL = 2;
-                            siteP0L = false;
-                        }
-                        if (site == L - 1) {
-                            const uint4 e = S.thrE[g2 * 2 + 1];
-                            aR = e.x;
-                            rR = e.y;
-                            kindR = 2;
-                            siteP0R = false;
-                        }
-                    }
-                }
-                // 0 reject, 1 accept, 2 undecided in FP32
-                int dR = tryR ? (x.y < aR ? 1 : (x.y > rR ? 0 : 2)) : 0;
-                int dL = tryL ? (x.w < aL ? 1 : (x.w > rL ? 0 : 2)) : 0;
-                if ((dR == 2 && siteP0R) || (dL == 2 && siteP0L)) {
-                    // refine with this site's own base probability
-                    const float P0k = (float)a.P0site[(int64_t)r2 * L + site];
-                    const float2 bi = S.zf[g2 * Z + z];
-                    const float lo = 1.0f - delta, hi = 1.0f + delta;
-                    if (dR == 2 && siteP0R && bi.y > 0.0f) {
-                        const float p = P0k * bi.y * bi.x;
-                        dR = x.y < acc_thr(p * lo) ? 1 : (x.y > rej_thr(p * hi) ? 0 : 2);
-                    }
-                    if (dL == 2 && siteP0L && bi.y > 0.0f) {
-                        const float p = P0k * bi.y;
-                        dL = x.w < acc_thr(p * lo) ? 1 : (x.w > rej_thr(p * hi) ? 0 : 2);
-                    }
-                }
-                if (dR == 2 || dL == 2) {
-                    double B, inv;
-                    exact_zone(S.Pb + g2 * (Z + 1), K, Z, L, a.N0[r2], Vd, z, &B, &inv);
-                    const double P0k = siteP0 ? a.P0site[(int64_t)r2 * L + site] : K->P0;
-                    if (dR == 2) {
-                        const double base = kindR == 1 ? K->E_in : (kindR == 2 ? K->E_out : P0k);
-                        const double p = __dmul_rn(__dmul_rn(base, inv), B);
-                        dR = exact_trial(((uint64_t)x.y << 32) | x.x, p, a.log, a.log_count,
-                                         a.log_cap, (int32_t)r2, t, site, 0, kindR)
-                                 ? 1
-                                 : 0;
-                        ++n_exact;
-                    }
-                    if (dL == 2) {
-                        const double base = kindL == 1 ? K->E_in : (kindL == 2 ? K->E_out : P0k);
-                        const double p = __dmul_rn(base, inv);
-                        dL = exact_trial(((uint64_t)x.w << 32) | x.z, p, a.log, a.log_count,
-                                         a.log_cap, (int32_t)r2, t, site, 1, kindL)
-                                 ? 1
-                                 : 0;
-                        ++n_exact;
-                    }
-                }
-                // X + M_right - M_left: both trials succeeding leaves the ion in place
-                if (dR == 1 && dL != 1) {
-                    moved = true;
-                    if (empty) S.inj[g2] = 1;  // injection into site 0
-                    else atomicOr(&S.mvR[g2 * LPR * WPL + (site >> 5)], 1u << (site & 31));
-                } else if (dL == 1 && dR != 1) {
-                    moved = true;
-                    if (empty) S.inj[G + g2] = 1;  // injection into site L-1
-                    else atomicOr(&S.mvL[g2 * LPR * WPL + (site >> 5)], 1u << (site & 31));
+            for (int i0 = lane; i0 < nlist; i0 += 64) {
+                const int i1 = i0 + 32;
+                const bool has1 = i1 < nlist;
+                const uint16_t d0 = S.list()[i0];
+                const uint16_t d1 = S.list()[has1 ? i1 : i0];
+                const int site0 = d0 & 0x7FF, g0 = d0 >> 11;
+                const int site1 = d1 & 0x7FF, g1 = d1 >> 11;
+                const uint4 x0 = philox((uint32_t)site0, (uint32_t)(rail0 + g0), t, a.instance,
+                                        a.rk0, a.rk1);
+                const uint4 x1 = philox((uint32_t)site1, (uint32_t)(rail0 + g1), t, a.instance,
+                                        a.rk0, a.rk1);
+                // electrode sites have their own entries after the G Z zone entries
+                const int ts0 = i0 >= n_inner ? G * Z + (i0 - n_inner) : g0 * Z + zone_tab[site0];
+                const int ts1 = i1 >= n_inner ? G * Z + (i1 - n_inner) : g1 * Z + zone_tab[site1];
+                const uint2 rm0 = S.rm()[ts0];
+                const uint2 rm1 = S.rm()[ts1];
+                const bool at0 = x0.y <= rm0.x || x0.w <= rm0.y;
+                const bool at1 = has1 && (x1.y <= rm1.x || x1.w <= rm1.y);
+                if (at0)
+                    moved |= slow_candidate<LPR, WPL>(S, a.self, i0, n_inner, rail0, t, zone_tab,
+                                                      persite, flo, fhi, false, x0.y, x0.w);
+                if (at1)
+                    moved |= slow_candidate<LPR, WPL>(S, a.self, i1, n_inner, rail0, t, zone_tab,
+                                                      persite, flo, fhi, false, x1.y, x1.w);
+            }
+            __syncwarp();
+
+            // ---- 5b. exact FP64 resolution of undecided candidates (rare)
+            const int nd = S.ndef()[0];
+            if (nd > 0) {
+                const bool overflow = nd > kDeferCap;
+                const int cnt2 = overflow ? nlist : nd;
+                for (int k = lane; k < cnt2; k += 32) {
+                    const int i = overflow ? k : (int)S.def()[k];
+                    moved |= slow_candidate<LPR, WPL>(S, a.self, i, n_inner, rail0, t, zone_tab,
+                                                      persite, flo, fhi, true, 0u, 0u);
                 }
             }
 
             // ---- 6. conflicts, synchronous update, current
-            if (__any_sync(FULL, moved)) {
+            dirty = __any_sync(FULL, moved);
+            if (dirty) {
                 __syncwarp();
                 uint32_t mR[WPL], mL[WPL], tR[WPL], tL[WPL], cf[WPL];
 #pragma unroll
                 for (int j = 0; j < WPL; ++j) {
-                    mR[j] = S.mvR[seg * LPR * WPL + wbase + j];
-                    mL[j] = S.mvL[seg * LPR * WPL + wbase + j];
+                    mR[j] = S.mvR()[seg * LPR * WPL + wbase + j];
+                    mL[j] = S.mvL()[seg * LPR * WPL + wbase + j];
                 }
-                const int iR = S.inj[seg], iL = S.inj[G + seg];
+                const int iR = S.inj()[seg], iL = S.inj()[G + seg];
                 const uint32_t mR_prev = __shfl_up_sync(FULL, mR[WPL - 1], 1, LPR);
                 const uint32_t mL_next = __shfl_down_sync(FULL, mL[0], 1, LPR);
 #pragma unroll
@@ -543,30 +723,32 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
                     tL[j] &= ~cf[j];
                     Jl += __popc(mL[j]) - __popc(mR[j]);
                     o[j] = (o[j] & ~(mR[j] | mL[j])) | tR[j] | tL[j];
-                    if (iR && firstm[j] && !(cf[j] & 1u)) Jl -= 1;          // injected at site 0
-                    if (iL && lastm[j] && !(cf[j] & lastm[j])) Jl += 1;     // injected at L-1
-                    n_move += (unsigned long long)(__popc(mR[j]) + __popc(mL[j]));
+                    n_move += (unsigned)(__popc(mR[j]) + __popc(mL[j]));
+                    if (iR && firstm[j] && !(cf[j] & 1u)) {          // injected at site 0
+                        Jl -= 1;
+                        n_move += 1;
+                    }
+                    if (iL && lastm[j] && !(cf[j] & lastm[j])) {     // injected at L-1
+                        Jl += 1;
+                        n_move += 1;
+                    }
                 }
-                if (iR && sl == 0 && !(cf[0] & 1u)) n_move += 1;
-#pragma unroll
-                for (int j = 0; j < WPL; ++j)
-                    if (iL && lastm[j] && !(cf[j] & lastm[j])) n_move += 1;
                 __syncwarp();
 #pragma unroll
                 for (int j = 0; j < WPL; ++j) {
-                    S.mvR[seg * LPR * WPL + wbase + j] = 0u;
-                    S.mvL[seg * LPR * WPL + wbase + j] = 0u;
+                    S.mvR()[seg * LPR * WPL + wbase + j] = 0u;
+                    S.mvL()[seg * LPR * WPL + wbase + j] = 0u;
                 }
                 if (sl == 0) {
-                    S.inj[seg] = 0;
-                    S.inj[G + seg] = 0;
+                    S.inj()[seg] = 0;
+                    S.inj()[G + seg] = 0;
                 }
                 const int Jw = __reduce_add_sync(FULL, Jl);
                 if (lane == 0 && Jw != 0) atomicAdd(&tr[0], Jw);
             }
             __syncwarp();
         }
-        // ---- flush this chunk's traces
+        // ---- flush this chunk's traces and counters
         __syncthreads();
         const int nval = (c1 - c0) * (1 + Z);
         for (int i = threadIdx.x; i < nval; i += blockDim.x) {
@@ -580,6 +762,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             }
             trace[i] = 0;
         }
+        const unsigned m = __reduce_add_sync(FULL, n_move);
+        if (lane == 0) {
+            if (n_draw) atomicAdd(&a.counters[0], (unsigned long long)n_draw);
+            if (m) atomicAdd(&a.counters[2], (unsigned long long)m);
+        }
+        n_draw = n_move = 0;
         __syncthreads();
     }
 
@@ -592,16 +780,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             if (s0 < a.stride) *(uint4 *)(wrow + s0) = unpack16(o[j] & 0xFFFFu);
             if (s0 + 16 < a.stride) *(uint4 *)(wrow + s0 + 16) = unpack16(o[j] >> 16);
         }
-    }
-    // ---- counters
-    if (lane == 0) {
-        if (n_draw) atomicAdd(&a.counters[0], n_draw);
-    }
-    n_exact = __reduce_add_sync(FULL, (unsigned)n_exact);
-    n_move = __reduce_add_sync(FULL, (unsigned)n_move);
-    if (lane == 0) {
-        if (n_exact) atomicAdd(&a.counters[1], n_exact);
-        if (n_move) atomicAdd(&a.counters[2], n_move);
     }
 }
 
@@ -621,11 +799,17 @@ cudaError_t smem_attr()
 
 }  // namespace
 
-size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush)
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite)
 {
-    const int G = 32 / lpr;
-    return (size_t)warps * warp_block_bytes(G, Z, wpl) + align16(sizeof(int32_t) * flush * (1 + Z)) +
-           align16((size_t)L);
+    size_t wb = 0;
+    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, persite);
+    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, persite);
+    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, persite);
+    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, persite);
+    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, persite);
+    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, persite);
+    else wb = Layout<32, 1>::bytes(Z, persite);
+    return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) + align16((size_t)L);
 }
 
 int sweep_pick_lpr(int L, int *wpl)

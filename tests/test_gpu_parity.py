@@ -199,3 +199,14 @@ def test_hysteresis_device_sampled_rails_full_size(kmc):
     z = np.array([oracle.zone_of(k, wl.device.L, wl.device.Z) for k in range(wl.device.L)])
     assert np.array_equal(Zg[0], np.bincount(z, weights=occ_init.sum(axis=0), minlength=10))
     sim.close()
+
+
+@pytest.mark.parametrize("L,electrodes", [(128, 0), (40, 1), (1024, 1)])
+def test_rapidly_varying_bias_bit_exact(kmc, L, electrodes):
+    # the bias jumps every step, so the FP32 bands must cover a wide voltage window
+    rng = np.random.default_rng(L)
+    dev = _dev(R=20, L=L, Z=8, electrodes=electrodes, k_e=2e6, rho_e=0.35)
+    occ0 = W.random_occupancy(20, L, 0.4, seed=L + 1)
+    V = rng.uniform(-4.0, 4.0, size=300)
+    V[::7] = 0.0
+    _compare(kmc, dev, V, occ0)
