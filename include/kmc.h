@@ -142,6 +142,45 @@ void kmc_destroy(kmc_handle *h);
 /* Message of the last failure on this thread ("" if none). */
 const char *kmc_last_error(void);
 
+/* ---- Sweep without any device allocation.
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: applications whose framework allocator owns
+ * all of the GPU's memory and forbids side allocations, latency-bound loops
+ * where cudaMalloc's implicit synchronisation is unacceptable, and services
+ * that must keep the device footprint fixed after start-up.
+ *
+ * Advances n_steps steps, starting at absolute step t0, of a device whose
+ * state is caller-owned device memory:
+ *   occ_dev          uint8 [n_rails][row_stride] occupancy (0/1 in the first
+ *                    n_sites bytes of each row; padding is rewritten as 0),
+ *                    16-byte aligned, row_stride a multiple of 16, updated in place;
+ *   N0_dev_or_null   int32 [n_rails] background ion count per rail (the count at
+ *                    the device's first step), or NULL to take it from occ_dev
+ *                    at this call (right for a device's first call, and for any
+ *                    call with blocking electrodes, where counts are conserved);
+ *   V_dev            double [n_steps]: V of steps t0 .. t0 + n_steps - 1;
+ *   J_dev            int64 [n_steps] output, as kmc_observables' J_out;
+ *   zone_counts_dev  int64 [n_steps][n_zones] output, as zone_counts_out.
+ * Only the scalar barrier Ea_eV is used (no per-site table); init_mode, n_ions
+ * and fill are ignored; the near-threshold log is not returned.  Results are
+ * identical to kmc_step_n on a handle in the same state.
+ *
+ * Working memory is one static device array of about 4 MiB that every GPU
+ * loading the library holds until the process exits; it limits n_rails to
+ * KMC_NOALLOC_MAX_RAILS (larger sizes return KMC_E_ARG).  The first call on
+ * a device looks up that array's device address and raises the kernels'
+ * shared-memory limit, so make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The entry point zeroes
+ * what has to start at zero (its counters, J_dev, zone_counts_dev) on
+ * cuda_stream, calls no allocator, and is asynchronous.  Errors: KMC_E_ARG or
+ * KMC_E_PROB before anything is launched, KMC_E_CUDA if a launch fails. */
+#define KMC_NOALLOC_MAX_RAILS (1 << 20)
+int kmc_sweep_noalloc(const kmc_params *params, uint8_t *occ_dev, int64_t row_stride,
+                      const int32_t *N0_dev_or_null, const double *V_dev, int64_t t0,
+                      int64_t n_steps, int64_t *J_dev, int64_t *zone_counts_dev,
+                      void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

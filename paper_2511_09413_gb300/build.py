@@ -1,6 +1,6 @@
 """Build libkmc.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Three translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2511_09413_gb300/libkmc.so``.  No cmake, no torch extension machinery.
 """
 from __future__ import annotations
@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkmc.so")
-SOURCES = ["kmc_sweep.cu", "kmc_setup.cu", "kmc_capi.cu"]
+SOURCES = ["kmc_sweep.cu", "kmc_setup.cu", "kmc_capi.cu", "kmc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -53,6 +53,8 @@ int cuda_fail(cudaError_t e, const char *what)
 
 }  // namespace
 
+void kmc::kmc_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }
+
 struct kmc_handle {
     kmc_params p{};
     cudaStream_t stream = nullptr;

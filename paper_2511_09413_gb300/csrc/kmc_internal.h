@@ -78,6 +78,9 @@ int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
 
+// Sets the message returned by kmc_last_error() on this thread (kmc_capi.cu).
+void kmc_internal_set_error(const char *msg);
+
 // setup kernels (kmc_setup.cu)
 cudaError_t setup_constants(const kmc_params &p, DevConst *K, cudaStream_t s);
 cudaError_t setup_p0_table(const kmc_params &p, const double *Ea, double *P0, int64_t n, int *bad,

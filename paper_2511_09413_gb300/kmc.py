@@ -68,7 +68,7 @@ kmc_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_
 # every symbol include/kmc.h declares
 EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "kmc_set_voltage",
            "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch", "kmc_current_step",
-           "kmc_destroy", "kmc_last_error"]
+           "kmc_destroy", "kmc_last_error", "kmc_sweep_noalloc"]
 
 _lib = None
 
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
     L.kmc_destroy.argtypes = [vp]
     L.kmc_destroy.restype = None
     L.kmc_last_error.restype = ctypes.c_char_p
+    L.kmc_sweep_noalloc.argtypes = [P(kmc_params), vp, i64, vp, vp, i64, i64, vp, vp, vp]
+    L.kmc_sweep_noalloc.restype = ctypes.c_int
     for name in ("kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables",
                  "kmc_set_voltage", "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch"):
         getattr(L, name).restype = ctypes.c_int
@@ -184,6 +186,18 @@ def kmc_destroy(h: int):
 
 def kmc_last_error() -> str:
     return load().kmc_last_error().decode(errors="replace")
+
+
+def kmc_sweep_noalloc(params: kmc_params, occ_dev: int, row_stride: int, N0_dev: Optional[int],
+                      V_dev: int, t0: int, n_steps: int, J_dev: int, zone_counts_dev: int,
+                      stream: int = 0):
+    """Advance caller-owned device state without allocating (device pointers
+    as integers, e.g. torch ``tensor.data_ptr()``); see include/kmc.h."""
+    _check(load().kmc_sweep_noalloc(ctypes.byref(params), ctypes.c_void_p(occ_dev), int(row_stride),
+                                    ctypes.c_void_p(N0_dev) if N0_dev else None,
+                                    ctypes.c_void_p(V_dev), int(t0), int(n_steps),
+                                    ctypes.c_void_p(J_dev), ctypes.c_void_p(zone_counts_dev),
+                                    ctypes.c_void_p(stream)))
 
 
 # ------------------------------------------------------------ conveniences
