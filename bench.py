@@ -52,6 +52,24 @@ def _peaks():
         return 6800.0, "fallback", SM_MAX_MHZ
 
 
+def _traffic_per_launch(rails: int):
+    """DRAM bytes (read + write) of one sweep launch from the ncu capture in
+    profiles/sweep_traffic.json, scaled to `rails` (the per-launch traffic is
+    the occupancy and per-site tables, proportional to rails x sites), or None
+    when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if sha != rec.get("kernel_source_sha256"):
+        return None
+    return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * rails / rec["rails"]
+
+
 def _env_rank():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -275,7 +293,8 @@ def run_kmc(args):
                        "parallelism": "one independent device per GPU" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "G Philox4x32-10 blocks/s", "frac": achieved / alu_peak,
-                         "traffic": None,
+                         "traffic": _traffic_per_launch(R),
+                         "traffic_unit": "DRAM bytes per launch (ncu, scaled by rails)",
                          "peak_basis": "%d SMs x %d IMAD lanes/clk x %.0f MHz / %d IMAD ops per block" % (
                              SMS, IMAD_PER_SM_PER_CLK, sm_max, PHILOX_IMAD),
                          "hbm_basis": {"achieved_GBps": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9,
