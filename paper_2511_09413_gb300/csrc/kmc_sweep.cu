@@ -40,6 +40,10 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kDeferCap = 64;           // deferred (exact-path) candidates per warp and step
 constexpr uint16_t kNoSite = 0xFFFFu;   // empty electrode slot of an inactive rail
+#ifndef KMC_DRAW_ILP
+#define KMC_DRAW_ILP 2
+#endif
+constexpr int kDrawIlp = KMC_DRAW_ILP;  // Philox blocks in flight per lane in the draw loop
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
 // multiplies; the high halves are xor-ed with the other counter words and the
@@ -645,30 +649,34 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
             // ---- 5. draws: two Philox blocks per lane per iteration; everything
             //         but the reject-sure test is on the slow path
             bool moved = false;
-            for (int i0 = lane; i0 < nlist; i0 += 64) {
-                const int i1 = i0 + 32;
-                const bool has1 = i1 < nlist;
-                const uint16_t d0 = S.list()[i0];
-                const uint16_t d1 = S.list()[has1 ? i1 : i0];
-                const int site0 = d0 & 0x7FF, g0 = d0 >> 11;
-                const int site1 = d1 & 0x7FF, g1 = d1 >> 11;
-                const uint4 x0 = philox((uint32_t)site0, (uint32_t)(rail0 + g0), t, a.instance,
-                                        a.rk0, a.rk1);
-                const uint4 x1 = philox((uint32_t)site1, (uint32_t)(rail0 + g1), t, a.instance,
-                                        a.rk0, a.rk1);
-                // electrode sites have their own entries after the G Z zone entries
-                const int ts0 = i0 >= n_inner ? G * Z + (i0 - n_inner) : g0 * Z + zone_tab[site0];
-                const int ts1 = i1 >= n_inner ? G * Z + (i1 - n_inner) : g1 * Z + zone_tab[site1];
-                const uint2 rm0 = S.rm()[ts0];
-                const uint2 rm1 = S.rm()[ts1];
-                const bool at0 = x0.y <= rm0.x || x0.w <= rm0.y;
-                const bool at1 = has1 && (x1.y <= rm1.x || x1.w <= rm1.y);
-                if (at0)
-                    moved |= slow_candidate<LPR, WPL>(S, a.self, i0, n_inner, rail0, t, zone_tab,
-                                                      persite, flo, fhi, false, x0.y, x0.w);
-                if (at1)
-                    moved |= slow_candidate<LPR, WPL>(S, a.self, i1, n_inner, rail0, t, zone_tab,
-                                                      persite, flo, fhi, false, x1.y, x1.w);
+            for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlp) {
+                // kDrawIlp independent Philox blocks per lane per iteration
+                uint32_t xy[kDrawIlp], xw[kDrawIlp];
+                bool at[kDrawIlp];
+#pragma unroll
+                for (int q = 0; q < kDrawIlp; ++q) {
+                    const int i = i0 + 32 * q;
+                    const bool has = i < nlist;
+                    const uint16_t d = S.list()[has ? i : i0];
+                    // with one rail per warp the rail slot is 0: the rail, step and
+                    // instance words are then warp-uniform and the compiler hoists
+                    // the parts of the first two Philox rounds that depend only on them
+                    const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
+                    const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, a.instance,
+                                           a.rk0, a.rk1);
+                    // electrode sites have their own entries after the G Z zone entries
+                    const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
+                    const uint2 rm = S.rm()[ts];
+                    xy[q] = x.y;
+                    xw[q] = x.w;
+                    at[q] = has && (x.y <= rm.x || x.w <= rm.y);
+                }
+#pragma unroll
+                for (int q = 0; q < kDrawIlp; ++q)
+                    if (at[q])
+                        moved |= slow_candidate<LPR, WPL>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
+                                                          zone_tab, persite, flo, fhi, false, xy[q],
+                                                          xw[q]);
             }
             __syncwarp();
 
