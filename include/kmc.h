@@ -142,6 +142,38 @@ void kmc_destroy(kmc_handle *h);
 /* Message of the last failure on this thread ("" if none). */
 const char *kmc_last_error(void);
 
+/* ---- Batches: many devices advanced by one persistent launch.
+ * A batch holds n_inst independent devices (each as kmc_create would make it,
+ * with its own sizes, parameters, voltage table and occupancy) that advance
+ * together.  Every launch covers all devices: CTAs take (device, rail tile)
+ * work items, longest tiles first, from a shared counter, so devices of very
+ * different sizes keep the GPU full.  A launch of steps_per_launch steps and
+ * the advance of the batch's step counter are captured once as a CUDA graph
+ * and replayed.  Results per device are identical to kmc_step_n on that
+ * device alone.  All devices share one seed (the Philox key) and are told
+ * apart by their instance words (counter word 3); give them distinct ones.
+ * V_per_step[i] is device i's host voltage table of n_steps_total entries;
+ * init_occ_or_null may be NULL or hold NULL entries (for init_mode != 2).
+ * Per-site barrier tables are not available in batches.  Errors as kmc_create. */
+typedef struct kmc_batch kmc_batch;
+int kmc_batch_create(const kmc_params *params, int32_t n_inst, const double *const *V_per_step,
+                     int64_t n_steps_total, const uint8_t *const *init_occ_or_null,
+                     void *cuda_stream, kmc_batch **out);
+/* Advance every device by n_steps (asynchronous on the batch's stream). */
+int kmc_batch_step_n(kmc_batch *b, int64_t n_steps);
+/* kmc_observables for device `inst` of the batch (synchronizes). */
+int kmc_batch_observables(kmc_batch *b, int32_t inst, int64_t first_step, int64_t count,
+                          int64_t *J_out, int64_t *zone_counts_out, uint8_t *occ_out_or_null);
+/* Launch shape: warps per CTA (1, 2, 4, 8) and steps per launch (graph size). */
+int kmc_batch_set_launch(kmc_batch *b, int32_t warps_per_cta, int32_t steps_per_launch);
+/* Autotuner: times every candidate launch shape (warps per CTA in {4, 8},
+ * steps per launch in {64 ... 2048} up to probe_steps) on probe_steps real
+ * steps from the current state, restores the state after each probe (the
+ * simulation is unchanged), and keeps the fastest.  Synchronizes. */
+int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_t *steps_out);
+int64_t kmc_batch_current_step(const kmc_batch *b);
+void kmc_batch_destroy(kmc_batch *b);
+
 /* ---- Sweep without any device allocation.
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory: applications whose framework allocator owns

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkmc.so")
-SOURCES = ["kmc_sweep.cu", "kmc_setup.cu", "kmc_capi.cu", "kmc_noalloc.cu"]
+SOURCES = ["kmc_sweep.cu", "kmc_setup.cu", "kmc_capi.cu", "kmc_noalloc.cu", "kmc_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

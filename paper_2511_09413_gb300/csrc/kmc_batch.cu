@@ -1,0 +1,403 @@
+// kmc_batch.cu -- many devices advanced together: one persistent launch per
+// chunk of steps over all devices' rail tiles, replayed as a CUDA graph, with
+// the CTA size and the steps per launch chosen by a measuring autotuner.
+//
+// Each device of a batch is an ordinary handle (kmc_create), so placement,
+// per-device constants and observables are exactly those of a single device;
+// the batch adds the work list, the shared step counter and the graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "kmc_handle.h"
+#include "kmc_internal.h"
+
+using namespace kmc;
+
+struct kmc_batch {
+    std::vector<kmc_handle *> dev;       // one handle per device
+    cudaStream_t user = nullptr;         // caller's stream
+    cudaStream_t work = nullptr;         // stream the graph is captured and replayed on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int64_t t = 0;                       // current absolute step
+    int64_t n_total = 0;
+    SweepArgs *inst = nullptr;           // device copies of the handles' arguments
+    BatchItem *items = nullptr;
+    unsigned *work_ctr = nullptr;
+    int64_t *t0 = nullptr;
+    int n_items = 0;
+    int warps = 8;
+    int steps_per_launch = 512;
+    int flush = 256;
+    size_t smem = 0;
+    int grid = 0;
+    uint32_t rk0[10], rk1[10];
+    cudaGraphExec_t graph = nullptr;     // one launch of steps_per_launch steps + advance
+    int graph_warps = 0, graph_steps = 0;
+};
+
+namespace {
+
+int fail(int code, const std::string &msg)
+{
+    kmc_internal_set_error(msg.c_str());
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? KMC_E_NOMEM : KMC_E_CUDA,
+                std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define BCK(call, what)                                    \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+void drop_graph(kmc_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_warps = b->graph_steps = 0;
+}
+
+// Work list for a CTA size: one item per tile of 32/LPR * warps rails, larger
+// tiles (longer rails) first so that the dynamic schedule ends evenly.
+int build_items(kmc_batch *b, int warps)
+{
+    if (b->work) cudaStreamSynchronize(b->work);   // launches in flight may read the old list
+    std::vector<BatchItem> items;
+    std::vector<int64_t> cost;
+    size_t smem = 0;
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (max_smem <= 0) max_smem = 48 * 1024;
+    max_smem = std::min(max_smem, 200 * 1024);
+    for (size_t i = 0; i < b->dev.size(); ++i) {
+        const kmc_params &p = b->dev[i]->p;
+        int wpl = 1;
+        const int lpr = sweep_pick_lpr(p.n_sites, &wpl);
+        const int G = 32 / lpr;
+        const int64_t tile = (int64_t)G * warps;
+        smem = std::max(smem, sweep_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, warps, b->flush,
+                                               b->dev[i]->P0site != nullptr));
+        for (int64_t r0 = 0; r0 < p.n_rails; r0 += tile) {
+            BatchItem it;
+            it.inst = (int32_t)i;
+            it.kind = sweep_kind(lpr, wpl);
+            it.tile_rail0 = r0;
+            items.push_back(it);
+            cost.push_back(std::min<int64_t>(tile, p.n_rails - r0) * p.n_sites);
+        }
+    }
+    if (smem + 1024 > (size_t)max_smem)
+        return fail(KMC_E_ARG, "batch: shared memory for this CTA size exceeds the device limit");
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<BatchItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    if (b->items) cudaFreeAsync(b->items, b->user);
+    b->items = nullptr;
+    BCK(cudaMallocAsync((void **)&b->items, sizeof(BatchItem) * std::max<size_t>(1, sorted.size()),
+                        b->user),
+        "cudaMallocAsync(items)");
+    BCK(cudaMemcpyAsync(b->items, sorted.data(), sizeof(BatchItem) * sorted.size(),
+                        cudaMemcpyHostToDevice, b->user),
+        "copy items");
+    BCK(cudaStreamSynchronize(b->user), "batch items");
+    b->n_items = (int)sorted.size();
+    b->smem = smem;
+    b->warps = warps;
+    // persistent grid: every SM full (3 CTAs of 8 warps, or more smaller ones)
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = std::max(1, 24 / warps);
+    b->grid = std::max(1, std::min(b->n_items, sms * per_sm));
+    drop_graph(b);
+    return KMC_OK;
+}
+
+BatchArgs batch_args(const kmc_batch *b, int n_steps)
+{
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.inst = b->inst;
+    a.items = b->items;
+    a.n_items = b->n_items;
+    a.n_steps = n_steps;
+    a.flush = b->flush;
+    a.work = b->work_ctr;
+    a.t0 = b->t0;
+    a.t0_mut = b->t0;
+    for (int i = 0; i < 10; ++i) {
+        a.rk0[i] = b->rk0[i];
+        a.rk1[i] = b->rk1[i];
+    }
+    return a;
+}
+
+// n_steps (<= 2^30) on the work stream: a graph replay when n_steps is the
+// tuned chunk, a direct launch otherwise.
+int run_chunk(kmc_batch *b, int n_steps)
+{
+    if (n_steps == b->steps_per_launch) {
+        if (!b->graph || b->graph_warps != b->warps || b->graph_steps != n_steps) {
+            drop_graph(b);
+            cudaGraph_t g = nullptr;
+            BCK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t le = batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem, b->work);
+            cudaError_t ce = cudaStreamEndCapture(b->work, &g);
+            if (le != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(le, "batched launch (capture)");
+            }
+            BCK(ce, "end capture");
+            cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            BCK(ie, "cudaGraphInstantiate");
+            b->graph_warps = b->warps;
+            b->graph_steps = n_steps;
+        }
+        BCK(cudaGraphLaunch(b->graph, b->work), "cudaGraphLaunch");
+        return KMC_OK;
+    }
+    BCK(batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem, b->work), "batched launch");
+    return KMC_OK;
+}
+
+int step_impl(kmc_batch *b, int64_t n_steps)
+{
+    BCK(cudaEventRecord(b->ev_in, b->user), "event");
+    BCK(cudaStreamWaitEvent(b->work, b->ev_in, 0), "wait");
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int n = (int)std::min<int64_t>(left, b->steps_per_launch);
+        int rc = run_chunk(b, n);
+        if (rc) return rc;
+        left -= n;
+    }
+    BCK(cudaEventRecord(b->ev_out, b->work), "event");
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0), "wait");
+    b->t += n_steps;
+    for (kmc_handle *h : b->dev) h->t = b->t;
+    return KMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kmc_batch_create(const kmc_params *params, int32_t n_inst, const double *const *V_per_step,
+                     int64_t n_steps_total, const uint8_t *const *init_occ_or_null,
+                     void *cuda_stream, kmc_batch **out)
+{
+    if (!out) return fail(KMC_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params || n_inst < 1) return fail(KMC_E_ARG, "batch needs params and n_inst >= 1");
+    if (!V_per_step) return fail(KMC_E_ARG, "V_per_step is NULL");
+    for (int i = 1; i < n_inst; ++i)
+        if (params[i].seed != params[0].seed)
+            return fail(KMC_E_ARG, "all devices of a batch share one seed (Philox key); "
+                                   "they are told apart by their instance words");
+    kmc_batch *b = new kmc_batch();
+    b->user = (cudaStream_t)cuda_stream;
+    b->n_total = n_steps_total;
+    int rc = KMC_OK;
+    for (int i = 0; i < n_inst && rc == KMC_OK; ++i) {
+        kmc_handle *h = nullptr;
+        rc = kmc_create(&params[i], V_per_step[i], n_steps_total,
+                        init_occ_or_null ? init_occ_or_null[i] : nullptr, nullptr, cuda_stream, &h);
+        if (rc == KMC_OK) b->dev.push_back(h);
+    }
+    auto bail = [&](int code) {
+        std::string msg = kmc_last_error();
+        kmc_batch_destroy(b);
+        kmc_internal_set_error(msg.c_str());
+        return code;
+    };
+    if (rc != KMC_OK) return bail(rc);
+    uint32_t k0 = (uint32_t)(params[0].seed & 0xffffffffu), k1 = (uint32_t)(params[0].seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        b->rk0[i] = k0;
+        b->rk1[i] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = batch_set_smem_limit()) != cudaSuccess)
+        return bail(cuda_fail(e, "batch streams"));
+    std::vector<SweepArgs> host(n_inst);
+    for (int i = 0; i < n_inst; ++i) host[i] = b->dev[i]->args;
+    if ((e = cudaMallocAsync((void **)&b->inst, sizeof(SweepArgs) * n_inst, b->user)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&b->work_ctr, sizeof(unsigned) * 4, b->user)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&b->t0, sizeof(int64_t) * 2, b->user)) != cudaSuccess)
+        return bail(cuda_fail(e, "batch allocation"));
+    if ((e = cudaMemcpyAsync(b->inst, host.data(), sizeof(SweepArgs) * n_inst, cudaMemcpyHostToDevice,
+                             b->user)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned) * 4, b->user)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->t0, 0, sizeof(int64_t) * 2, b->user)) != cudaSuccess)
+        return bail(cuda_fail(e, "batch set-up"));
+    rc = build_items(b, b->warps);
+    if (rc) return bail(rc);
+    *out = b;
+    return KMC_OK;
+}
+
+int kmc_batch_step_n(kmc_batch *b, int64_t n_steps)
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (n_steps < 0) return fail(KMC_E_ARG, "n_steps must be >= 0");
+    if (b->t + n_steps > b->n_total)
+        return fail(KMC_E_RANGE, "steps exceed the voltage tables of the batch");
+    if (n_steps == 0) return KMC_OK;
+    return step_impl(b, n_steps);
+}
+
+int kmc_batch_observables(kmc_batch *b, int32_t inst, int64_t first_step, int64_t count,
+                          int64_t *J_out, int64_t *zone_counts_out, uint8_t *occ_out_or_null)
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (inst < 0 || inst >= (int32_t)b->dev.size()) return fail(KMC_E_ARG, "device index out of range");
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    return kmc_observables(b->dev[inst], first_step, count, J_out, zone_counts_out, occ_out_or_null);
+}
+
+int kmc_batch_set_launch(kmc_batch *b, int32_t warps_per_cta, int32_t steps_per_launch)
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)
+        return fail(KMC_E_ARG, "warps_per_cta must be 1, 2, 4 or 8");
+    if (steps_per_launch < 1 || steps_per_launch > (1 << 20))
+        return fail(KMC_E_ARG, "steps_per_launch must be in [1, 2^20]");
+    b->steps_per_launch = steps_per_launch;
+    if (warps_per_cta != b->warps) return build_items(b, warps_per_cta);
+    drop_graph(b);
+    return KMC_OK;
+}
+
+int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_t *steps_out)
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (probe_steps < 1) return fail(KMC_E_ARG, "probe_steps must be >= 1");
+    if (b->t + probe_steps > b->n_total)
+        return fail(KMC_E_RANGE, "probe steps exceed the voltage tables of the batch");
+    // save every device's state (occupancy and counters); the probes advance
+    // real steps from it and it is restored after every probe
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    std::vector<void *> saved(b->dev.size(), nullptr);
+    auto cleanup = [&]() {
+        for (void *p : saved)
+            if (p) cudaFreeAsync(p, b->user);
+        cudaStreamSynchronize(b->user);
+    };
+    for (size_t i = 0; i < b->dev.size(); ++i) {
+        kmc_handle *h = b->dev[i];
+        const size_t bytes = (size_t)h->stride * h->p.n_rails + sizeof(unsigned long long) * 8;
+        if ((e = cudaMallocAsync(&saved[i], bytes, b->user)) != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "tune: save buffer");
+        }
+        cudaMemcpyAsync(saved[i], h->occ, (size_t)h->stride * h->p.n_rails,
+                        cudaMemcpyDeviceToDevice, b->user);
+        cudaMemcpyAsync((char *)saved[i] + (size_t)h->stride * h->p.n_rails, h->misc,
+                        sizeof(unsigned long long) * 8, cudaMemcpyDeviceToDevice, b->user);
+    }
+    auto restore = [&]() {
+        cudaStreamSynchronize(b->work);
+        for (size_t i = 0; i < b->dev.size(); ++i) {
+            kmc_handle *h = b->dev[i];
+            cudaMemcpyAsync(h->occ, saved[i], (size_t)h->stride * h->p.n_rails,
+                            cudaMemcpyDeviceToDevice, b->user);
+            cudaMemcpyAsync(h->misc, (char *)saved[i] + (size_t)h->stride * h->p.n_rails,
+                            sizeof(unsigned long long) * 8, cudaMemcpyDeviceToDevice, b->user);
+            cudaMemsetAsync(h->J + b->t, 0, sizeof(int64_t) * (size_t)probe_steps, b->user);
+            cudaMemsetAsync(h->Zc + b->t * h->p.n_zones, 0,
+                            sizeof(int64_t) * (size_t)probe_steps * h->p.n_zones, b->user);
+        }
+        const int64_t t = b->t;
+        cudaMemcpyAsync(b->t0, &t, sizeof(int64_t), cudaMemcpyHostToDevice, b->user);
+        cudaStreamSynchronize(b->user);
+    };
+    const int cand_warps[] = {4, 8};
+    const int cand_steps[] = {64, 128, 256, 512, 1024, 2048};
+    double best = -1.0;
+    int best_w = b->warps, best_s = b->steps_per_launch;
+    const int64_t t_start = b->t;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int w : cand_warps) {
+        int rc = build_items(b, w);
+        if (rc) continue;  // this CTA size does not fit
+        for (int sp : cand_steps) {
+            if (sp > probe_steps) continue;
+            b->steps_per_launch = sp;
+            const int64_t n = probe_steps / sp * sp;
+            run_chunk(b, sp);  // warm-up (captures the graph)
+            restore();
+            cudaEventRecord(e0, b->work);
+            for (int64_t k = 0; k < n; k += sp) run_chunk(b, sp);
+            cudaEventRecord(e1, b->work);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double rate = (double)n / (ms > 0 ? ms : 1e-3);
+            if (rate > best) {
+                best = rate;
+                best_w = w;
+                best_s = sp;
+            }
+            restore();
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->t = t_start;
+    cleanup();
+    b->steps_per_launch = best_s;
+    int rc = build_items(b, best_w);
+    if (rc) return rc;
+    if (warps_out) *warps_out = best_w;
+    if (steps_out) *steps_out = best_s;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tune");
+    return KMC_OK;
+}
+
+int64_t kmc_batch_current_step(const kmc_batch *b) { return b ? b->t : -1; }
+
+void kmc_batch_destroy(kmc_batch *b)
+{
+    if (!b) return;
+    if (b->user) cudaStreamSynchronize(b->user);
+    if (b->work) cudaStreamSynchronize(b->work);
+    drop_graph(b);
+    cudaStream_t s = b->user;
+    if (b->inst) cudaFreeAsync(b->inst, s);
+    if (b->items) cudaFreeAsync(b->items, s);
+    if (b->work_ctr) cudaFreeAsync(b->work_ctr, s);
+    if (b->t0) cudaFreeAsync(b->t0, s);
+    cudaStreamSynchronize(s);
+    for (kmc_handle *h : b->dev) kmc_destroy(h);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->work) cudaStreamDestroy(b->work);
+    delete b;
+}
+
+}  // extern "C"

@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "kmc_handle.h"
 #include "kmc_internal.h"
 
 using namespace kmc;
@@ -23,11 +24,6 @@ namespace {
 
 thread_local std::string g_err;
 
-struct Allocator {
-    kmc_alloc_fn alloc = nullptr;
-    kmc_free_fn free_fn = nullptr;
-    void *ctx = nullptr;
-};
 Allocator g_alloc;
 std::mutex g_alloc_mu;
 std::once_flag g_attr_once;
@@ -55,57 +51,6 @@ int cuda_fail(cudaError_t e, const char *what)
 
 void kmc::kmc_internal_set_error(const char *msg) { g_err = msg ? msg : ""; }
 
-struct kmc_handle {
-    kmc_params p{};
-    cudaStream_t stream = nullptr;
-    int64_t n_total = 0;
-    int64_t t = 0;
-    int64_t stride = 0;
-    Allocator al;
-    std::vector<std::pair<void *, size_t>> allocs;
-
-    uint8_t *occ = nullptr;
-    double *V = nullptr;
-    int32_t *N0 = nullptr;
-    double *P0site = nullptr;
-    float *P0f = nullptr;
-    float2 *P0bnd = nullptr;
-    DevConst *K = nullptr;
-    unsigned long long *J = nullptr;
-    unsigned long long *Zc = nullptr;
-    kmc_log_entry *log = nullptr;
-    unsigned long long *misc = nullptr;  // [0] log count, [1..3] counters, [4] scratch count
-    SweepArgs *args_dev = nullptr;       // device copy of args for the kernels' rare paths
-    int64_t log_cap = 4096;
-
-    SweepArgs args{};
-    SweepLaunch launch{};
-    int warps_req = 0;
-    int flush_req = 0;
-
-    void *alloc(size_t bytes)
-    {
-        void *ptr = nullptr;
-        if (bytes == 0) bytes = 16;
-        if (al.alloc) {
-            ptr = al.alloc(bytes, (void *)stream, al.ctx);
-        } else if (cudaMallocAsync(&ptr, bytes, stream) != cudaSuccess) {
-            cudaGetLastError();
-            ptr = nullptr;
-        }
-        if (ptr) allocs.emplace_back(ptr, bytes);
-        return ptr;
-    }
-    void release_all()
-    {
-        for (auto &a : allocs) {
-            if (al.free_fn) al.free_fn(a.first, a.second, (void *)stream, al.ctx);
-            else cudaFreeAsync(a.first, stream);
-        }
-        allocs.clear();
-        cudaStreamSynchronize(stream);
-    }
-};
 
 namespace {
 

@@ -1,0 +1,74 @@
+// kmc_handle.h -- host-side state of one device (one kmc_handle) shared by
+// the single-device runtime (kmc_capi.cu) and the batch runtime (kmc_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+#include <vector>
+
+#include "kmc_internal.h"
+
+namespace kmc {
+
+// Device allocator in effect when a handle was created.
+struct Allocator {
+    kmc_alloc_fn alloc = nullptr;
+    kmc_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+};
+
+}  // namespace kmc
+
+struct kmc_handle {
+    kmc_params p{};
+    cudaStream_t stream = nullptr;
+    int64_t n_total = 0;
+    int64_t t = 0;
+    int64_t stride = 0;
+    kmc::Allocator al;
+    std::vector<std::pair<void *, size_t>> allocs;
+
+    uint8_t *occ = nullptr;
+    double *V = nullptr;
+    int32_t *N0 = nullptr;
+    double *P0site = nullptr;
+    float *P0f = nullptr;
+    float2 *P0bnd = nullptr;
+    kmc::DevConst *K = nullptr;
+    unsigned long long *J = nullptr;
+    unsigned long long *Zc = nullptr;
+    kmc_log_entry *log = nullptr;
+    unsigned long long *misc = nullptr;  // [0] log count, [1..3] counters, [4] scratch count
+    kmc::SweepArgs *args_dev = nullptr;       // device copy of args for the kernels' rare paths
+    int64_t log_cap = 4096;
+
+    kmc::SweepArgs args{};
+    kmc::SweepLaunch launch{};
+    int warps_req = 0;
+    int flush_req = 0;
+
+    void *alloc(size_t bytes)
+    {
+        void *ptr = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (al.alloc) {
+            ptr = al.alloc(bytes, (void *)stream, al.ctx);
+        } else if (cudaMallocAsync(&ptr, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+        }
+        if (ptr) allocs.emplace_back(ptr, bytes);
+        return ptr;
+    }
+    void release_all()
+    {
+        for (auto &a : allocs) {
+            if (al.free_fn) al.free_fn(a.first, a.second, (void *)stream, al.ctx);
+            else cudaFreeAsync(a.first, stream);
+        }
+        allocs.clear();
+        cudaStreamSynchronize(stream);
+    }
+};

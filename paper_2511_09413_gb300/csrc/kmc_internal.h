@@ -64,6 +64,27 @@ struct SweepArgs {
     float E_inf, E_outf;          // electrode base probabilities in FP32
 };
 
+// One work item of a batched launch: a tile of rails of one device.
+struct BatchItem {
+    int32_t inst;        // device index in the batch
+    int32_t kind;        // kernel shape (sweep_kind of the device's lanes per rail)
+    int64_t tile_rail0;  // first rail of the tile
+};
+
+// Arguments of one batched launch.
+struct BatchArgs {
+    const SweepArgs *inst;   // [n_inst] per-device arguments (device memory)
+    const BatchItem *items;  // [n_items] in scheduling order
+    int32_t n_items;
+    int32_t n_steps;         // steps of this launch
+    int32_t flush;           // steps between trace flushes
+    int32_t pad;
+    unsigned *work;          // next work item (reset by the advance kernel)
+    const int64_t *t0;       // absolute step of the launch's first step
+    int64_t *t0_mut;         // the same counter, advanced after the launch
+    uint32_t rk0[10], rk1[10];
+};
+
 // Launch configuration chosen on the host.
 struct SweepLaunch {
     int lpr;      // lanes per rail (1..32)
@@ -77,6 +98,10 @@ size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bo
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
+int sweep_kind(int lpr, int wpl);
+cudaError_t batch_set_smem_limit();
+// launches the batched sweep and then advances *t0 by n_steps and re-arms work
+cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s);
 
 // Sets the message returned by kmc_last_error() on this thread (kmc_capi.cu).
 void kmc_internal_set_error(const char *msg);

@@ -356,14 +356,17 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
 }
 
 template <int LPR, int WPL>
-// 80 registers (3 CTAs of 256 threads per SM): the draw loop fits; the exact
-// FP64 path, which runs for about one draw in a million, may spill.
-__global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
+// One CTA's tile of rails advanced through steps [t0, t0 + n_steps): the whole
+// sweep of S2.1.2 - S2.1.7 for rails [tile_rail0, tile_rail0 + G * warps).
+// `a` describes one device (in the kernel's parameter space for a single
+// device, in shared memory for a batch); rk0 / rk1 are the Philox round keys.
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *rk0,
+                                           const uint32_t *rk1, int64_t t0, int n_steps,
+                                           int flush, int64_t tile_rail0, uint8_t *smem)
 {
     constexpr int G = 32 / LPR;
     constexpr int LSEG = 32 * LPR * WPL;  // site capacity of one rail slot
     constexpr int VWIN = 32;              // steps per voltage window of the FP32 bounds
-    extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -371,9 +374,10 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
     const int sl = lane % LPR;
     const int wbase = sl * WPL;
     const int L = a.L, Z = a.Z;
+    const uint32_t instance = a.instance;
     const bool open = a.electrodes == 1;
     const bool persite = a.P0bnd != nullptr;
-    const int64_t rail0 = ((int64_t)blockIdx.x * nwarps + warp) * G;
+    const int64_t rail0 = tile_rail0 + (int64_t)warp * G;
     const int64_t rail = rail0 + seg;
     const bool active = rail < a.R;
     const int nact = (int)max((int64_t)0, min((int64_t)G, (int64_t)a.R - rail0));
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
     S.gz = (uint32_t)Ly::gz8(Z);
     S.pbz = (uint32_t)Ly::pb_bytes(Z);
     int32_t *trace = (int32_t *)(smem + (size_t)nwarps * wb);
-    uint8_t *zone_tab = (uint8_t *)(trace + (size_t)a.flush * (1 + Z));
+    uint8_t *zone_tab = (uint8_t *)(trace + (size_t)flush * (1 + Z));
 
     // ---- per-CTA tables and per-warp staging
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
         while (a.bnd[z + 1] <= k) ++z;
         zone_tab[k] = (uint8_t)z;
     }
-    for (int i = threadIdx.x; i < a.flush * (1 + Z); i += blockDim.x) trace[i] = 0;
+    for (int i = threadIdx.x; i < flush * (1 + Z); i += blockDim.x) trace[i] = 0;
     for (int i = lane; i < 32 * WPL; i += 32) {
         S.mvR()[i] = 0;
         S.mvL()[i] = 0;
@@ -452,10 +456,10 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
     unsigned n_draw = 0, n_move = 0;
     __syncthreads();
 
-    for (int c0 = 0; c0 < a.n_steps; c0 += a.flush) {
-        const int c1 = min(a.n_steps, c0 + a.flush);
+    for (int c0 = 0; c0 < n_steps; c0 += flush) {
+        const int c1 = min(n_steps, c0 + flush);
         for (int s = c0; s < c1; ++s) {
-            const uint32_t t = (uint32_t)(a.t0 + s);
+            const uint32_t t = (uint32_t)(t0 + s);
             int32_t *tr = trace + (s - c0) * (1 + Z);
 
             if (dirty) {
@@ -560,7 +564,7 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
             //         every step of the voltage window while the occupancy holds
             if (dirty || s >= win_end) {
                 if (s >= win_end) {
-                    win_end = min(s + VWIN, a.n_steps);
+                    win_end = min(s + VWIN, n_steps);
                     const int k = min(lane, win_end - 1 - s);
                     const double v = a.V[t + k];
                     float vlo = __double2float_rd(v), vhi = __double2float_ru(v);
@@ -662,8 +666,8 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
                     // instance words are then warp-uniform and the compiler hoists
                     // the parts of the first two Philox rounds that depend only on them
                     const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
-                    const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, a.instance,
-                                           a.rk0, a.rk1);
+                    const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
+                                           rk0, rk1);
                     // electrode sites have their own entries after the G Z zone entries
                     const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
                     const uint2 rm = S.rm()[ts];
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
         for (int i = threadIdx.x; i < nval; i += blockDim.x) {
             const int v = trace[i];
             if (v != 0) {
-                const int64_t step = a.t0 + c0 + i / (1 + Z);
+                const int64_t step = t0 + c0 + i / (1 + Z);
                 const int q = i % (1 + Z);
                 const unsigned long long add = (unsigned long long)(long long)v;
                 if (q == 0) atomicAdd(&a.J[step], add);
@@ -788,6 +792,58 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
             if (s0 < a.stride) *(uint4 *)(wrow + s0) = unpack16(o[j] & 0xFFFFu);
             if (s0 + 16 < a.stride) *(uint4 *)(wrow + s0 + 16) = unpack16(o[j] >> 16);
         }
+    }
+}
+
+template <int LPR, int WPL>
+// 80 registers (3 CTAs of 256 threads per SM): the draw loop fits; the exact
+// FP64 path, which runs for about one draw in a million, may spill.
+__global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);
+    sweep_tile<LPR, WPL>(a, a.rk0, a.rk1, a.t0, a.n_steps, a.flush, tile_rail0, smem);
+}
+
+// Batch of devices in one persistent launch: CTAs take (device, rail tile)
+// work items from a shared counter and run the same tile body with that
+// device's arguments copied to shared memory.  The step index lives in device
+// memory so that a launch and its advance can be replayed as a CUDA graph.
+__global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs b)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ SweepArgs ia;
+    __shared__ int s_item;
+    const int64_t t0 = *b.t0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.work, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.n_items) break;
+        const BatchItem it = b.items[item];
+        const uint32_t *src = (const uint32_t *)&b.inst[it.inst];
+        for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs) / 4); i += blockDim.x)
+            ((uint32_t *)&ia)[i] = src[i];
+        __syncthreads();
+        switch (it.kind) {
+        case 0: sweep_tile<1, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 1: sweep_tile<2, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 2: sweep_tile<4, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 3: sweep_tile<8, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 4: sweep_tile<16, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 5: sweep_tile<32, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        default: sweep_tile<32, 2>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        }
+        __syncthreads();
+    }
+}
+
+// Advance the batch's step counter and re-arm its work counter.
+__global__ void batch_advance_kernel(int64_t *t0, unsigned *work, int n_steps)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *t0 += n_steps;
+        *work = 0u;
     }
 }
 
@@ -844,6 +900,34 @@ cudaError_t sweep_set_smem_limits()
     if ((r = smem_attr<32, 1>()) != cudaSuccess) e = r;
     if ((r = smem_attr<32, 2>()) != cudaSuccess) e = r;
     return e;
+}
+
+int sweep_kind(int lpr, int wpl)
+{
+    if (wpl == 2) return 6;
+    switch (lpr) {
+    case 1: return 0;
+    case 2: return 1;
+    case 4: return 2;
+    case 8: return 3;
+    case 16: return 4;
+    default: return 5;
+    }
+}
+
+cudaError_t batch_set_smem_limit()
+{
+    return cudaFuncSetAttribute(sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+}
+
+cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s)
+{
+    sweep_batch_kernel<<<grid, warps * 32, smem, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_advance_kernel<<<1, 32, 0, s>>>(b.t0_mut, b.work, b.n_steps);
+    return cudaGetLastError();
 }
 
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s)

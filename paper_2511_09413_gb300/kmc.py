@@ -68,7 +68,9 @@ kmc_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_
 # every symbol include/kmc.h declares
 EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "kmc_set_voltage",
            "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch", "kmc_current_step",
-           "kmc_destroy", "kmc_last_error", "kmc_sweep_noalloc"]
+           "kmc_destroy", "kmc_last_error", "kmc_sweep_noalloc", "kmc_batch_create",
+           "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
+           "kmc_batch_current_step", "kmc_batch_destroy"]
 
 _lib = None
 
@@ -101,6 +103,20 @@ def load(path: str = LIB_PATH):
     L.kmc_last_error.restype = ctypes.c_char_p
     L.kmc_sweep_noalloc.argtypes = [P(kmc_params), vp, i64, vp, vp, i64, i64, vp, vp, vp]
     L.kmc_sweep_noalloc.restype = ctypes.c_int
+    L.kmc_batch_create.argtypes = [P(kmc_params), ctypes.c_int32, P(P(ctypes.c_double)), i64,
+                                   P(P(ctypes.c_uint8)), vp, P(vp)]
+    L.kmc_batch_step_n.argtypes = [vp, i64]
+    L.kmc_batch_observables.argtypes = [vp, ctypes.c_int32, i64, i64, P(ctypes.c_int64),
+                                        P(ctypes.c_int64), P(ctypes.c_uint8)]
+    L.kmc_batch_set_launch.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    L.kmc_batch_tune.argtypes = [vp, i64, P(ctypes.c_int32), P(ctypes.c_int32)]
+    L.kmc_batch_current_step.argtypes = [vp]
+    L.kmc_batch_current_step.restype = i64
+    L.kmc_batch_destroy.argtypes = [vp]
+    L.kmc_batch_destroy.restype = None
+    for name in ("kmc_batch_create", "kmc_batch_step_n", "kmc_batch_observables",
+                 "kmc_batch_set_launch", "kmc_batch_tune"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables",
                  "kmc_set_voltage", "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch"):
         getattr(L, name).restype = ctypes.c_int
@@ -280,6 +296,114 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             kmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- batches
+
+def kmc_batch_create(params_list, V_list, init_occ_list=None, stream: int = 0) -> int:
+    n = len(params_list)
+    P = (kmc_params * n)(*params_list)
+    Vs = [np.ascontiguousarray(v, dtype=np.float64) for v in V_list]
+    n_total = Vs[0].shape[0]
+    if any(v.shape[0] != n_total for v in Vs):
+        raise ValueError("all voltage tables of a batch have the same length")
+    Vp = (ctypes.POINTER(ctypes.c_double) * n)(*[_ptr(v, ctypes.c_double) for v in Vs])
+    occs = None
+    Op = None
+    if init_occ_list is not None:
+        occs = [None if o is None else np.ascontiguousarray(o, dtype=np.uint8) for o in init_occ_list]
+        Op = (ctypes.POINTER(ctypes.c_uint8) * n)(*[_ptr(o, ctypes.c_uint8) for o in occs])
+    h = ctypes.c_void_p()
+    _check(load().kmc_batch_create(P, n, Vp, n_total, Op, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def kmc_batch_step_n(b: int, n_steps: int):
+    _check(load().kmc_batch_step_n(ctypes.c_void_p(b), int(n_steps)))
+
+
+def kmc_batch_observables(b: int, inst: int, first_step: int, count: int,
+                          J_out: Optional[np.ndarray], zone_counts_out: Optional[np.ndarray],
+                          occ_out: Optional[np.ndarray]):
+    _check(load().kmc_batch_observables(ctypes.c_void_p(b), int(inst), int(first_step), int(count),
+                                        _ptr(J_out, ctypes.c_int64),
+                                        _ptr(zone_counts_out, ctypes.c_int64),
+                                        _ptr(occ_out, ctypes.c_uint8)))
+
+
+def kmc_batch_set_launch(b: int, warps_per_cta: int, steps_per_launch: int):
+    _check(load().kmc_batch_set_launch(ctypes.c_void_p(b), int(warps_per_cta), int(steps_per_launch)))
+
+
+def kmc_batch_tune(b: int, probe_steps: int):
+    w = ctypes.c_int32()
+    st = ctypes.c_int32()
+    _check(load().kmc_batch_tune(ctypes.c_void_p(b), int(probe_steps), ctypes.byref(w),
+                                 ctypes.byref(st)))
+    return w.value, st.value
+
+
+def kmc_batch_current_step(b: int) -> int:
+    return int(load().kmc_batch_current_step(ctypes.c_void_p(b)))
+
+
+def kmc_batch_destroy(b: int):
+    load().kmc_batch_destroy(ctypes.c_void_p(b))
+
+
+class Batch:
+    """Many devices advanced together by one persistent launch per chunk."""
+
+    def __init__(self, devs, Vs, init_modes, n_ions=None, fills=None, occ0s=None,
+                 stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        n = len(devs)
+        n_ions = n_ions or [0] * n
+        fills = fills or [0.0] * n
+        self.params = [params_from_device(d, m, ni, f)
+                       for d, m, ni, f in zip(devs, init_modes, n_ions, fills)]
+        self.shapes = [(p.n_rails, p.n_sites, p.n_zones) for p in self.params]
+        self.h = kmc_batch_create(self.params, Vs, occ0s, stream)
+
+    @property
+    def t(self) -> int:
+        return kmc_batch_current_step(self.h)
+
+    def step_n(self, n: int):
+        kmc_batch_step_n(self.h, n)
+
+    def tune(self, probe_steps: int):
+        return kmc_batch_tune(self.h, probe_steps)
+
+    def set_launch(self, warps_per_cta: int, steps_per_launch: int):
+        kmc_batch_set_launch(self.h, warps_per_cta, steps_per_launch)
+
+    def traces(self, inst: int, first: int = 0, count: Optional[int] = None):
+        R, L, Z = self.shapes[inst]
+        count = self.t - first if count is None else count
+        J = np.zeros(count, dtype=np.int64)
+        Zc = np.zeros((count, Z), dtype=np.int64)
+        kmc_batch_observables(self.h, inst, first, count, J, Zc, None)
+        return J, Zc
+
+    def occupancy(self, inst: int) -> np.ndarray:
+        R, L, Z = self.shapes[inst]
+        occ = np.zeros((R, L), dtype=np.uint8)
+        kmc_batch_observables(self.h, inst, 0, 0, None, None, occ)
+        return occ
+
+    def close(self):
+        if getattr(self, "h", None):
+            kmc_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
