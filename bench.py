@@ -320,12 +320,77 @@ def run_kmc(args):
     return 0
 
 
+def run_batched(args):
+    """Batched STDP devices (512 by default) in one persistent launch per chunk,
+    against the same devices advanced one after another by the single-device
+    kernel: equal work, hence equal ensemble error."""
+    import torch
+    from paper_2511_09413_gb300 import kmc
+
+    torch.cuda.set_device(0)
+    kmc.load()
+    chunk = args.chunk
+    n_steps = (args.warmup + args.steps) * chunk + args.probe
+    devs, Vs, fills, delays = W.stdp_batch(args.instances, n_steps=n_steps)
+    n = len(devs)
+    sites = sum(d.R * d.L for d in devs)
+    stream = torch.cuda.current_stream()
+    b = kmc.Batch(devs, Vs, [1] * n, fills=fills, stream=stream.cuda_stream)
+    warps, spl = b.tune(args.probe)
+    acc = b.accept_path
+    for _ in range(args.warmup):
+        b.step_n(chunk)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.step_n(chunk)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = sites * chunk * args.steps / (ms / 1e3)
+    b.close()
+    # the same devices, one at a time, single-device kernel
+    plain_ms = 0.0
+    for d, V, f in zip(devs, Vs, fills):
+        sim = kmc.Sim(d, V, init_mode=1, fill=f, stream=stream.cuda_stream)
+        sim.step_n(chunk)                      # warm-up
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        sim.step_n(chunk)
+        a1.record(stream)
+        a1.synchronize()
+        plain_ms += a0.elapsed_time(a1)
+        sim.close()
+    plain_value = sites * chunk / (plain_ms / 1e3)
+    line = {
+        "metric": METRIC + ", batched", "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "stdp_batch", "devices": n, "sites_total": sites,
+                   "rails": "log-uniform [256, 16384]", "sites_per_rail": "log-uniform [128, 2048]",
+                   "fill": "U(0.05, 0.4)", "protocol": "spike pair, 1 V 1 ms pulses, 2000 steps/ms",
+                   "time_steps_per_step": chunk, "tuned": {"warps_per_cta": warps,
+                                                           "steps_per_launch": spl,
+                                                           "accept_path": acc}},
+        "plain_one_device_at_a_time": {"value": plain_value, "unit": UNIT,
+                                       "speedup_batched": value / plain_value},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kmc", "reference"], default="kmc")
+    ap.add_argument("--workload", choices=["hysteresis", "batched"], default="hysteresis")
+    ap.add_argument("--instances", type=int, default=512, help="devices in the batched workload")
+    ap.add_argument("--probe", type=int, default=1024, help="autotuner probe steps (batched)")
     ap.add_argument("--chunk", type=int, default=1000, help="time steps per benchmark step")
     ap.add_argument("--rails", type=int, default=65536)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -337,6 +402,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_kmc(args)
 
 

@@ -133,6 +133,15 @@ int kmc_counters(kmc_handle *h, uint64_t out[3]);
  * trace flushes (1..1024, 0 = automatic).  Results do not depend on either. */
 int kmc_set_launch(kmc_handle *h, int warps_per_cta, int flush_steps);
 
+/* Accept path: mode 1 selects the kernel that also keeps accept-sure bounds
+ * per zone and decides inner hops whose draw is not rejected outright inside
+ * the draw loop (faster where P0 is of order 1e-2 or more), 0 the kernel
+ * without them, -1 (the default) picks 1 when P0 at the device's Ea is at
+ * least 1/128.  Results do not depend on the mode (every decision is still
+ * u <= p in FP64, Eq. 5-6).  kmc_accept_path returns the mode in effect. */
+int kmc_set_accept_path(kmc_handle *h, int mode);
+int kmc_accept_path(const kmc_handle *h);
+
 /* Current absolute step of the handle. */
 int64_t kmc_current_step(const kmc_handle *h);
 
@@ -167,10 +176,17 @@ int kmc_batch_observables(kmc_batch *b, int32_t inst, int64_t first_step, int64_
 /* Launch shape: warps per CTA (1, 2, 4, 8) and steps per launch (graph size). */
 int kmc_batch_set_launch(kmc_batch *b, int32_t warps_per_cta, int32_t steps_per_launch);
 /* Autotuner: times every candidate launch shape (warps per CTA in {4, 8},
- * steps per launch in {64 ... 2048} up to probe_steps) on probe_steps real
+ * steps per launch in {64 ... 2048} up to probe_steps, and the accept path,
+ * see below) on probe_steps real
  * steps from the current state, restores the state after each probe (the
  * simulation is unchanged), and keeps the fastest.  Synchronizes. */
 int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_t *steps_out);
+/* Accept path of the batch kernel (as kmc_set_accept_path; automatic mode
+ * looks at the largest P0 of the batch).  With the automatic mode,
+ * kmc_batch_tune also times the other kernel at the best shape and keeps it
+ * when faster.  kmc_batch_accept_path returns the mode in effect. */
+int kmc_batch_set_accept_path(kmc_batch *b, int32_t mode);
+int kmc_batch_accept_path(const kmc_batch *b);
 int64_t kmc_batch_current_step(const kmc_batch *b);
 void kmc_batch_destroy(kmc_batch *b);
 

@@ -34,11 +34,13 @@ struct kmc_batch {
     int warps = 8;
     int steps_per_launch = 512;
     int flush = 256;
+    int acc_req = -1;                    // accept path: -1 automatic, 0 off, 1 on
+    int acc = 0;                         // accept path in effect
     size_t smem = 0;
     int grid = 0;
     uint32_t rk0[10], rk1[10];
     cudaGraphExec_t graph = nullptr;     // one launch of steps_per_launch steps + advance
-    int graph_warps = 0, graph_steps = 0;
+    int graph_warps = 0, graph_steps = 0, graph_acc = -1;
 };
 
 namespace {
@@ -66,6 +68,7 @@ void drop_graph(kmc_batch *b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     b->graph_warps = b->graph_steps = 0;
+    b->graph_acc = -1;
 }
 
 // Work list for a CTA size: one item per tile of 32/LPR * warps rails, larger
@@ -81,6 +84,9 @@ int build_items(kmc_batch *b, int warps)
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (max_smem <= 0) max_smem = 48 * 1024;
     max_smem = std::min(max_smem, 200 * 1024);
+    float p0max = 0.0f;
+    for (const kmc_handle *h : b->dev) p0max = std::max(p0max, h->args.P0f_scalar);
+    const int acc = b->acc_req >= 0 ? b->acc_req : (p0max >= kAcceptAutoP0 ? 1 : 0);
     for (size_t i = 0; i < b->dev.size(); ++i) {
         const kmc_params &p = b->dev[i]->p;
         int wpl = 1;
@@ -88,7 +94,7 @@ int build_items(kmc_batch *b, int warps)
         const int G = 32 / lpr;
         const int64_t tile = (int64_t)G * warps;
         smem = std::max(smem, sweep_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, warps, b->flush,
-                                               b->dev[i]->P0site != nullptr));
+                                               b->dev[i]->P0site != nullptr, acc != 0));
         for (int64_t r0 = 0; r0 < p.n_rails; r0 += tile) {
             BatchItem it;
             it.inst = (int32_t)i;
@@ -118,6 +124,7 @@ int build_items(kmc_batch *b, int warps)
     b->n_items = (int)sorted.size();
     b->smem = smem;
     b->warps = warps;
+    b->acc = acc;
     // persistent grid: every SM full (3 CTAs of 8 warps, or more smaller ones)
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -151,11 +158,13 @@ BatchArgs batch_args(const kmc_batch *b, int n_steps)
 int run_chunk(kmc_batch *b, int n_steps)
 {
     if (n_steps == b->steps_per_launch) {
-        if (!b->graph || b->graph_warps != b->warps || b->graph_steps != n_steps) {
+        if (!b->graph || b->graph_warps != b->warps || b->graph_steps != n_steps ||
+            b->graph_acc != b->acc) {
             drop_graph(b);
             cudaGraph_t g = nullptr;
             BCK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal), "begin capture");
-            cudaError_t le = batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem, b->work);
+            cudaError_t le = batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem,
+                                          b->acc != 0, b->work);
             cudaError_t ce = cudaStreamEndCapture(b->work, &g);
             if (le != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -167,11 +176,13 @@ int run_chunk(kmc_batch *b, int n_steps)
             BCK(ie, "cudaGraphInstantiate");
             b->graph_warps = b->warps;
             b->graph_steps = n_steps;
+            b->graph_acc = b->acc;
         }
         BCK(cudaGraphLaunch(b->graph, b->work), "cudaGraphLaunch");
         return KMC_OK;
     }
-    BCK(batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem, b->work), "batched launch");
+    BCK(batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem, b->acc != 0, b->work),
+        "batched launch");
     return KMC_OK;
 }
 
@@ -338,38 +349,55 @@ int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_
     double best = -1.0;
     int best_w = b->warps, best_s = b->steps_per_launch;
     const int64_t t_start = b->t;
+    const int acc_req = b->acc_req;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // steps per second of the current items at sp steps per launch
+    auto probe = [&](int sp) {
+        b->steps_per_launch = sp;
+        const int64_t n = probe_steps / sp * sp;
+        run_chunk(b, sp);  // warm-up (captures the graph)
+        restore();
+        cudaEventRecord(e0, b->work);
+        for (int64_t k = 0; k < n; k += sp) run_chunk(b, sp);
+        cudaEventRecord(e1, b->work);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        restore();
+        return (double)n / (ms > 0 ? ms : 1e-3);
+    };
     for (int w : cand_warps) {
         int rc = build_items(b, w);
         if (rc) continue;  // this CTA size does not fit
         for (int sp : cand_steps) {
             if (sp > probe_steps) continue;
-            b->steps_per_launch = sp;
-            const int64_t n = probe_steps / sp * sp;
-            run_chunk(b, sp);  // warm-up (captures the graph)
-            restore();
-            cudaEventRecord(e0, b->work);
-            for (int64_t k = 0; k < n; k += sp) run_chunk(b, sp);
-            cudaEventRecord(e1, b->work);
-            cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double rate = (double)n / (ms > 0 ? ms : 1e-3);
+            const double rate = probe(sp);
             if (rate > best) {
                 best = rate;
                 best_w = w;
                 best_s = sp;
             }
-            restore();
         }
+    }
+    // with the automatic accept path, try the other kernel at the best shape
+    int best_acc = -1;
+    if (acc_req < 0 && best > 0.0) {
+        int rc = build_items(b, best_w);
+        const int auto_acc = b->acc;
+        if (rc == KMC_OK) {
+            b->acc_req = 1 - auto_acc;
+            if (build_items(b, best_w) == KMC_OK && probe(best_s) > best) best_acc = 1 - auto_acc;
+        }
+        b->acc_req = acc_req;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->t = t_start;
     cleanup();
     b->steps_per_launch = best_s;
+    if (best_acc >= 0) b->acc_req = best_acc;
     int rc = build_items(b, best_w);
     if (rc) return rc;
     if (warps_out) *warps_out = best_w;
@@ -378,6 +406,16 @@ int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_
     if (e != cudaSuccess) return cuda_fail(e, "tune");
     return KMC_OK;
 }
+
+int kmc_batch_set_accept_path(kmc_batch *b, int32_t mode)
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (mode < -1 || mode > 1) return fail(KMC_E_ARG, "mode must be -1, 0 or 1");
+    b->acc_req = mode;
+    return build_items(b, b->warps);
+}
+
+int kmc_batch_accept_path(const kmc_batch *b) { return b ? b->acc : -1; }
 
 int64_t kmc_batch_current_step(const kmc_batch *b) { return b ? b->t : -1; }
 

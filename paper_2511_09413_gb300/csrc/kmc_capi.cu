@@ -124,14 +124,16 @@ int pick_launch(kmc_handle *h)
     if (max_smem <= 0) max_smem = 48 * 1024;
     max_smem = std::min(max_smem, 200 * 1024);
     const bool ps = h->P0site != nullptr;
-    while (warps > 1 &&
-           sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps) > (size_t)max_smem)
+    l.acc = h->accept_req >= 0 ? h->accept_req : (h->args.P0f_scalar >= kAcceptAutoP0 ? 1 : 0);
+    const bool acc = l.acc != 0;
+    while (warps > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps,
+                                         acc) > (size_t)max_smem)
         warps >>= 1;
-    while (flush > 1 &&
-           sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps) > (size_t)max_smem)
+    while (flush > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps,
+                                         acc) > (size_t)max_smem)
         flush >>= 1;
     l.warps = warps;
-    l.smem = sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps);
+    l.smem = sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps, acc);
     const int64_t rails_per_cta = (int64_t)G * warps;
     l.grid = (int)((p.n_rails + rails_per_cta - 1) / rails_per_cta);
     h->launch = l;
@@ -472,6 +474,16 @@ int kmc_set_launch(kmc_handle *h, int warps_per_cta, int flush_steps)
     h->flush_req = flush_steps;
     return pick_launch(h);
 }
+
+int kmc_set_accept_path(kmc_handle *h, int mode)
+{
+    if (!h) return fail(KMC_E_ARG, "handle is NULL");
+    if (mode < -1 || mode > 1) return fail(KMC_E_ARG, "mode must be -1, 0 or 1");
+    h->accept_req = mode;
+    return pick_launch(h);
+}
+
+int kmc_accept_path(const kmc_handle *h) { return h ? h->launch.acc : -1; }
 
 int64_t kmc_current_step(const kmc_handle *h) { return h ? h->t : -1; }
 

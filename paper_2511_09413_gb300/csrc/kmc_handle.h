@@ -48,6 +48,7 @@ struct kmc_handle {
     kmc::SweepLaunch launch{};
     int warps_req = 0;
     int flush_req = 0;
+    int accept_req = -1;   // accept path: -1 automatic, 0 off, 1 on
 
     void *alloc(size_t bytes)
     {

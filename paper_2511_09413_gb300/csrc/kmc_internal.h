@@ -92,16 +92,23 @@ struct SweepLaunch {
     int warps;    // warps per CTA
     size_t smem;  // dynamic shared memory bytes
     int grid;
+    int acc;      // 1: kernel with accept-sure tables and the inline accept path
 };
 
-size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite);
+// Automatic choice of the accept path: on when the scalar hop probability P0
+// (Eq. 1 at the device's mean barrier) is at least this large.
+constexpr double kAcceptAutoP0 = 1.0 / 128.0;
+
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite,
+                        bool acc);
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
 int sweep_kind(int lpr, int wpl);
 cudaError_t batch_set_smem_limit();
 // launches the batched sweep and then advances *t0 by n_steps and re-arms work
-cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s);
+cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, bool acc,
+                         cudaStream_t s);
 
 // Sets the message returned by kmc_last_error() on this thread (kmc_capi.cu).
 void kmc_internal_set_error(const char *msg);

@@ -210,12 +210,16 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     if (max_smem <= 0) max_smem = 48 * 1024;
     max_smem = std::min(max_smem, 200 * 1024);
     int warps = 8, flush = 256;
-    while (warps > 1 && sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false) > (size_t)max_smem)
+    l.acc = P0 >= kAcceptAutoP0 ? 1 : 0;
+    const bool acc = l.acc != 0;
+    while (warps > 1 &&
+           sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false, acc) > (size_t)max_smem)
         warps >>= 1;
-    while (flush > 1 && sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false) > (size_t)max_smem)
+    while (flush > 1 &&
+           sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false, acc) > (size_t)max_smem)
         flush >>= 1;
     l.warps = warps;
-    l.smem = sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false);
+    l.smem = sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false, acc);
     const int64_t rails_per_cta = (int64_t)(32 / l.lpr) * warps;
     l.grid = (int)((R + rails_per_cta - 1) / rails_per_cta);
     a.flush = flush;

@@ -122,15 +122,19 @@ struct Layout {
     static constexpr size_t DEF = NDEF + 16;                   // uint16 [kDeferCap]
     static constexpr size_t LST = DEF + align16(2 * 64);       // uint16 [LIST]
     static constexpr size_t FIXED = LST + align16(2 * LIST);
-    // variable part: rm uint2 [G Z + 2 G] (zones, then the two electrode sites of
-    // each rail), zf and P0b float2 [G][Z] (gz8 = align16(8 G Z) bytes each),
+    // variable part: rm [G Z + 2 G] (zones, then the two electrode sites of each
+    // rail): uint2 reject-sure bounds (R, L) on the draw's high word, or, with the
+    // accept tables, uint4 (reject R, reject L, accept R, accept L), zf and P0b float2 [G][Z] (gz8 = align16(8 G Z) bytes each),
     // Pb int [G][Z+1], then P0f float [G][32 LPR WPL] (per-site mode only)
-    __host__ __device__ static size_t rm_bytes(int Z) { return align16((size_t)8 * G * (Z + 2)); }
+    __host__ __device__ static size_t rm_bytes(int Z, bool acc)
+    {
+        return align16((size_t)(acc ? 16 : 8) * G * (Z + 2));
+    }
     __host__ __device__ static size_t gz8(int Z) { return align16((size_t)8 * G * Z); }
     __host__ __device__ static size_t pb_bytes(int Z) { return align16((size_t)4 * G * (Z + 1)); }
-    __host__ __device__ static size_t bytes(int Z, bool persite)
+    __host__ __device__ static size_t bytes(int Z, bool persite, bool acc)
     {
-        return FIXED + rm_bytes(Z) + 2 * gz8(Z) + pb_bytes(Z) +
+        return FIXED + rm_bytes(Z, acc) + 2 * gz8(Z) + pb_bytes(Z) +
                (persite ? align16((size_t)4 * 1024 * WPL) : 0);
     }
 };
@@ -139,7 +143,7 @@ template <int LPR, int WPL>
 struct WarpSmem {
     using Ly = Layout<LPR, WPL>;
     uint8_t *b;     // block base (shared memory)
-    uint32_t rz;    // Layout::rm_bytes(Z)
+    uint32_t rz;    // Layout::rm_bytes(Z, acc)
     uint32_t gz;    // Layout::gz8(Z)
     uint32_t pbz;   // Layout::pb_bytes(Z)
     __device__ uint32_t *mvR() const { return (uint32_t *)(b + Ly::MVR); }
@@ -157,6 +161,7 @@ struct WarpSmem {
     __device__ uint16_t *def() const { return (uint16_t *)(b + Ly::DEF); }
     __device__ uint16_t *list() const { return (uint16_t *)(b + Ly::LST); }
     __device__ uint2 *rm() const { return (uint2 *)(b + Ly::FIXED); }
+    __device__ uint4 *rm4() const { return (uint4 *)(b + Ly::FIXED); }
     __device__ float2 *zf() const { return (float2 *)(b + Ly::FIXED + rz); }
     __device__ float2 *P0b() const { return (float2 *)(b + Ly::FIXED + rz + gz); }
     __device__ int32_t *Pb() const { return (int32_t *)(b + Ly::FIXED + rz + 2 * gz); }
@@ -355,11 +360,15 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
     return record_move<LPR, WPL>(S, D, g2);
 }
 
-template <int LPR, int WPL>
+template <int LPR, int WPL, bool ACC>
 // One CTA's tile of rails advanced through steps [t0, t0 + n_steps): the whole
 // sweep of S2.1.2 - S2.1.7 for rails [tile_rail0, tile_rail0 + G * warps).
 // `a` describes one device (in the kernel's parameter space for a single
 // device, in shared memory for a batch); rk0 / rk1 are the Philox round keys.
+// ACC adds accept-sure bounds to the zone tables and decides inner hops whose
+// draw is not rejected outright inside the draw loop; it pays when hop
+// probabilities are large (P0 of order 1e-2 and above), where most steps
+// carry several such draws per warp, and costs a few per cent otherwise.
 __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *rk0,
                                            const uint32_t *rk1, int64_t t0, int n_steps,
                                            int flush, int64_t tile_rail0, uint8_t *smem)
@@ -383,10 +392,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     const int nact = (int)max((int64_t)0, min((int64_t)G, (int64_t)a.R - rail0));
 
     using Ly = Layout<LPR, WPL>;
-    const size_t wb = Ly::bytes(Z, persite);
+    const size_t wb = Ly::bytes(Z, persite, ACC);
     WarpSmem<LPR, WPL> S;
     S.b = smem + (size_t)warp * wb;
-    S.rz = (uint32_t)Ly::rm_bytes(Z);
+    S.rz = (uint32_t)Ly::rm_bytes(Z, ACC);
     S.gz = (uint32_t)Ly::gz8(Z);
     S.pbz = (uint32_t)Ly::pb_bytes(Z);
     int32_t *trace = (int32_t *)(smem + (size_t)nwarps * wb);
@@ -589,7 +598,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     const int g2 = pi / Z;
                     const int z = pi - g2 * Z;
                     float2 zf = make_float2(0.0f, 0.0f);
-                    uint2 rm = make_uint2(FULL, FULL);
+                    uint4 rm = make_uint4(FULL, FULL, 0u, 0u);
                     if (g2 < nact) {
                         const int Pz = S.Pb()[g2 * (Z + 1) + z];
                         const int Pz1 = S.Pb()[g2 * (Z + 1) + z + 1];
@@ -600,15 +609,25 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         if (fabsf(x) <= 40.0f) {
                             const float B = __expf(x);
                             const float inv = __fdividef(1.0f, 1.0f + B);
-                            float bhi = a.P0f_scalar;
-                            if (persite) bhi = S.P0b()[pi].y;
-                            rm = make_uint2(rej_thr(bhi * inv * B * fhi), rej_thr(bhi * inv * fhi));
+                            float blo = a.P0f_scalar, bhi = a.P0f_scalar;
+                            if (persite) {
+                                const float2 pb = S.P0b()[pi];
+                                blo = pb.x;
+                                bhi = pb.y;
+                            }
+                            rm.x = rej_thr(bhi * inv * B * fhi);
+                            rm.y = rej_thr(bhi * inv * fhi);
+                            if constexpr (ACC) {
+                                rm.z = acc_thr(blo * inv * B * flo);
+                                rm.w = acc_thr(blo * inv * flo);
+                            }
                             zf = make_float2(B, inv);
                         }
                     }
                     // rm: reject-sure bounds for inner hops; (FULL, FULL) sends every
                     // draw of the zone to the slow path (zf == 0 marks it undecidable)
-                    S.rm()[pi] = rm;
+                    if constexpr (ACC) S.rm4()[pi] = rm;
+                    else S.rm()[pi] = make_uint2(rm.x, rm.y);
                     S.zf()[pi] = zf;
                     if (open && g2 < nact && (z == 0 || z == Z - 1)) {
                         // reject-sure bounds of the electrode sites: an occupied site 0
@@ -623,14 +642,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                             const bool occ0 = (S.ow()[g2 * LPR * WPL] & 1u) != 0;
                             uint2 e = occ0 ? make_uint2(rej_thr(bhi * sR * fhi), rej_thr(Eout * sL * fhi))
                                            : make_uint2(rej_thr(Ein * sR * fhi), 0u);
-                            S.rm()[G * Z + 2 * g2] = ok ? e : make_uint2(FULL, FULL);
+                            if (!ok) e = make_uint2(FULL, FULL);
+                            if constexpr (ACC) S.rm4()[G * Z + 2 * g2] = make_uint4(e.x, e.y, 0u, 0u);
+                            else S.rm()[G * Z + 2 * g2] = e;
                         }
                         if (z == Z - 1) {
                             const int wl = g2 * LPR * WPL + ((L - 1) >> 5);
                             const bool occl = (S.ow()[wl] >> ((L - 1) & 31)) & 1u;
                             uint2 e = occl ? make_uint2(rej_thr(Eout * sR * fhi), rej_thr(bhi * sL * fhi))
                                            : make_uint2(0u, rej_thr(Ein * sL * fhi));
-                            S.rm()[G * Z + 2 * g2 + 1] = ok ? e : make_uint2(FULL, FULL);
+                            if (!ok) e = make_uint2(FULL, FULL);
+                            if constexpr (ACC) S.rm4()[G * Z + 2 * g2 + 1] = make_uint4(e.x, e.y, 0u, 0u);
+                            else S.rm()[G * Z + 2 * g2 + 1] = e;
                         }
                     }
                 }
@@ -653,34 +676,88 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             // ---- 5. draws: two Philox blocks per lane per iteration; everything
             //         but the reject-sure test is on the slow path
             bool moved = false;
-            for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlp) {
-                // kDrawIlp independent Philox blocks per lane per iteration
-                uint32_t xy[kDrawIlp], xw[kDrawIlp];
-                bool at[kDrawIlp];
+            if constexpr (ACC) {
+                for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlp) {
+                    uint32_t xy[kDrawIlp], xw[kDrawIlp];
+                    uint4 th[kDrawIlp];
+                    int sites[kDrawIlp], gs[kDrawIlp];
+                    bool at[kDrawIlp];
 #pragma unroll
-                for (int q = 0; q < kDrawIlp; ++q) {
-                    const int i = i0 + 32 * q;
-                    const bool has = i < nlist;
-                    const uint16_t d = S.list()[has ? i : i0];
-                    // with one rail per warp the rail slot is 0: the rail, step and
-                    // instance words are then warp-uniform and the compiler hoists
-                    // the parts of the first two Philox rounds that depend only on them
-                    const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
-                    const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
-                                           rk0, rk1);
-                    // electrode sites have their own entries after the G Z zone entries
-                    const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
-                    const uint2 rm = S.rm()[ts];
-                    xy[q] = x.y;
-                    xw[q] = x.w;
-                    at[q] = has && (x.y <= rm.x || x.w <= rm.y);
+                    for (int q = 0; q < kDrawIlp; ++q) {
+                        const int i = i0 + 32 * q;
+                        const bool has = i < nlist;
+                        const uint16_t d = S.list()[has ? i : i0];
+                        const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
+                        const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
+                                               rk0, rk1);
+                        const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
+                        th[q] = S.rm4()[ts];
+                        xy[q] = x.y;
+                        xw[q] = x.w;
+                        sites[q] = site;
+                        gs[q] = g;
+                        at[q] = has && (x.y <= th[q].x || x.w <= th[q].y);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kDrawIlp; ++q) {
+                        if (!at[q]) continue;
+                        const int i = i0 + 32 * q;
+                        bool slow = i >= n_inner;   // electrode sites
+                        if (!slow) {
+                            // inner hop (the site is occupied): accept-sure and
+                            // reject-sure bounds of the zone and the free neighbours
+                            const int idx = gs[q] * LPR * WPL + (sites[q] >> 5);
+                            const uint32_t bit = 1u << (sites[q] & 31);
+                            const bool tR = (S.fR()[idx] & bit) != 0;
+                            const bool tL = (S.fL()[idx] & bit) != 0;
+                            const int dR = tR ? (xy[q] < th[q].z ? 1 : (xy[q] > th[q].x ? 0 : 2)) : 0;
+                            const int dL = tL ? (xw[q] < th[q].w ? 1 : (xw[q] > th[q].y ? 0 : 2)) : 0;
+                            if (dR == 2 || dL == 2) {
+                                slow = true;        // per-site refinement or the exact pass
+                            } else if (dR == 1 && dL != 1) {
+                                atomicOr(&S.mvR()[idx], bit);
+                                moved = true;
+                            } else if (dL == 1 && dR != 1) {
+                                atomicOr(&S.mvL()[idx], bit);
+                                moved = true;
+                            }                       // both accepted: the ion stays
+                        }
+                        if (slow)
+                            moved |= slow_candidate<LPR, WPL>(S, a.self, i, n_inner, rail0, t,
+                                                              zone_tab, persite, flo, fhi, false,
+                                                              xy[q], xw[q]);
+                    }
                 }
-#pragma unroll
-                for (int q = 0; q < kDrawIlp; ++q)
-                    if (at[q])
-                        moved |= slow_candidate<LPR, WPL>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
-                                                          zone_tab, persite, flo, fhi, false, xy[q],
-                                                          xw[q]);
+            } else {
+                for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlp) {
+                    // kDrawIlp independent Philox blocks per lane per iteration
+                    uint32_t xy[kDrawIlp], xw[kDrawIlp];
+                    bool at[kDrawIlp];
+    #pragma unroll
+                    for (int q = 0; q < kDrawIlp; ++q) {
+                        const int i = i0 + 32 * q;
+                        const bool has = i < nlist;
+                        const uint16_t d = S.list()[has ? i : i0];
+                        // with one rail per warp the rail slot is 0: the rail, step and
+                        // instance words are then warp-uniform and the compiler hoists
+                        // the parts of the first two Philox rounds that depend only on them
+                        const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
+                        const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
+                                               rk0, rk1);
+                        // electrode sites have their own entries after the G Z zone entries
+                        const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
+                        const uint2 rm = S.rm()[ts];
+                        xy[q] = x.y;
+                        xw[q] = x.w;
+                        at[q] = has && (x.y <= rm.x || x.w <= rm.y);
+                    }
+    #pragma unroll
+                    for (int q = 0; q < kDrawIlp; ++q)
+                        if (at[q])
+                            moved |= slow_candidate<LPR, WPL>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
+                                                              zone_tab, persite, flo, fhi, false, xy[q],
+                                                              xw[q]);
+                }
             }
             __syncwarp();
 
@@ -795,20 +872,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     }
 }
 
-template <int LPR, int WPL>
+template <int LPR, int WPL, bool ACC>
 // 80 registers (3 CTAs of 256 threads per SM): the draw loop fits; the exact
 // FP64 path, which runs for about one draw in a million, may spill.
 __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);
-    sweep_tile<LPR, WPL>(a, a.rk0, a.rk1, a.t0, a.n_steps, a.flush, tile_rail0, smem);
+    sweep_tile<LPR, WPL, ACC>(a, a.rk0, a.rk1, a.t0, a.n_steps, a.flush, tile_rail0, smem);
 }
 
 // Batch of devices in one persistent launch: CTAs take (device, rail tile)
 // work items from a shared counter and run the same tile body with that
 // device's arguments copied to shared memory.  The step index lives in device
 // memory so that a launch and its advance can be replayed as a CUDA graph.
+template <bool ACC>
 __global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -826,13 +904,13 @@ __global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs b)
             ((uint32_t *)&ia)[i] = src[i];
         __syncthreads();
         switch (it.kind) {
-        case 0: sweep_tile<1, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 1: sweep_tile<2, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 2: sweep_tile<4, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 3: sweep_tile<8, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 4: sweep_tile<16, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 5: sweep_tile<32, 1>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        default: sweep_tile<32, 2>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 0: sweep_tile<1, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 1: sweep_tile<2, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 2: sweep_tile<4, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 3: sweep_tile<8, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 4: sweep_tile<16, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        case 5: sweep_tile<32, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
+        default: sweep_tile<32, 2, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
         }
         __syncthreads();
     }
@@ -850,29 +928,33 @@ __global__ void batch_advance_kernel(int64_t *t0, unsigned *work, int n_steps)
 template <int LPR, int WPL>
 cudaError_t launch_t(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s)
 {
-    sweep_kernel<LPR, WPL><<<l.grid, l.warps * 32, l.smem, s>>>(a);
+    if (l.acc) sweep_kernel<LPR, WPL, true><<<l.grid, l.warps * 32, l.smem, s>>>(a);
+    else sweep_kernel<LPR, WPL, false><<<l.grid, l.warps * 32, l.smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int LPR, int WPL>
 cudaError_t smem_attr()
 {
-    return cudaFuncSetAttribute(sweep_kernel<LPR, WPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<LPR, WPL, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_kernel<LPR, WPL, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite)
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite, bool acc)
 {
     size_t wb = 0;
-    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, persite);
-    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, persite);
-    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, persite);
-    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, persite);
-    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, persite);
-    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, persite);
-    else wb = Layout<32, 1>::bytes(Z, persite);
+    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, persite, acc);
+    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, persite, acc);
+    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, persite, acc);
+    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, persite, acc);
+    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, persite, acc);
+    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, persite, acc);
+    else wb = Layout<32, 1>::bytes(Z, persite, acc);
     return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) + align16((size_t)L);
 }
 
@@ -917,13 +999,18 @@ int sweep_kind(int lpr, int wpl)
 
 cudaError_t batch_set_smem_limit()
 {
-    return cudaFuncSetAttribute(sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_batch_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s)
+cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, bool acc,
+                         cudaStream_t s)
 {
-    sweep_batch_kernel<<<grid, warps * 32, smem, s>>>(b);
+    if (acc) sweep_batch_kernel<true><<<grid, warps * 32, smem, s>>>(b);
+    else sweep_batch_kernel<false><<<grid, warps * 32, smem, s>>>(b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     batch_advance_kernel<<<1, 32, 0, s>>>(b.t0_mut, b.work, b.n_steps);

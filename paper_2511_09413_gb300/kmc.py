@@ -70,7 +70,8 @@ EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "
            "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch", "kmc_current_step",
            "kmc_destroy", "kmc_last_error", "kmc_sweep_noalloc", "kmc_batch_create",
            "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
-           "kmc_batch_current_step", "kmc_batch_destroy"]
+           "kmc_batch_current_step", "kmc_batch_destroy", "kmc_set_accept_path",
+           "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path"]
 
 _lib = None
 
@@ -114,8 +115,13 @@ def load(path: str = LIB_PATH):
     L.kmc_batch_current_step.restype = i64
     L.kmc_batch_destroy.argtypes = [vp]
     L.kmc_batch_destroy.restype = None
+    L.kmc_set_accept_path.argtypes = [vp, ctypes.c_int]
+    L.kmc_accept_path.argtypes = [vp]
+    L.kmc_batch_set_accept_path.argtypes = [vp, ctypes.c_int32]
+    L.kmc_batch_accept_path.argtypes = [vp]
     for name in ("kmc_batch_create", "kmc_batch_step_n", "kmc_batch_observables",
-                 "kmc_batch_set_launch", "kmc_batch_tune"):
+                 "kmc_batch_set_launch", "kmc_batch_tune", "kmc_set_accept_path",
+                 "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables",
                  "kmc_set_voltage", "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch"):
@@ -190,6 +196,14 @@ def kmc_counters(h: int) -> np.ndarray:
 
 def kmc_set_launch(h: int, warps_per_cta: int = 0, flush_steps: int = 0):
     _check(load().kmc_set_launch(ctypes.c_void_p(h), int(warps_per_cta), int(flush_steps)))
+
+
+def kmc_set_accept_path(h: int, mode: int = -1):
+    _check(load().kmc_set_accept_path(ctypes.c_void_p(h), int(mode)))
+
+
+def kmc_accept_path(h: int) -> int:
+    return int(load().kmc_accept_path(ctypes.c_void_p(h)))
 
 
 def kmc_current_step(h: int) -> int:
@@ -293,6 +307,13 @@ class Sim:
     def set_launch(self, warps_per_cta: int = 0, flush_steps: int = 0):
         kmc_set_launch(self.h, warps_per_cta, flush_steps)
 
+    def set_accept_path(self, mode: int = -1):
+        kmc_set_accept_path(self.h, mode)
+
+    @property
+    def accept_path(self) -> int:
+        return kmc_accept_path(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             kmc_destroy(self.h)
@@ -350,6 +371,14 @@ def kmc_batch_tune(b: int, probe_steps: int):
     return w.value, st.value
 
 
+def kmc_batch_set_accept_path(b: int, mode: int = -1):
+    _check(load().kmc_batch_set_accept_path(ctypes.c_void_p(b), int(mode)))
+
+
+def kmc_batch_accept_path(b: int) -> int:
+    return int(load().kmc_batch_accept_path(ctypes.c_void_p(b)))
+
+
 def kmc_batch_current_step(b: int) -> int:
     return int(load().kmc_batch_current_step(ctypes.c_void_p(b)))
 
@@ -386,6 +415,13 @@ class Batch:
 
     def set_launch(self, warps_per_cta: int, steps_per_launch: int):
         kmc_batch_set_launch(self.h, warps_per_cta, steps_per_launch)
+
+    def set_accept_path(self, mode: int = -1):
+        kmc_batch_set_accept_path(self.h, mode)
+
+    @property
+    def accept_path(self) -> int:
+        return kmc_batch_accept_path(self.h)
 
     def traces(self, inst: int, first: int = 0, count: Optional[int] = None):
         R, L, Z = self.shapes[inst]

@@ -91,6 +91,21 @@ def constant_protocol(V: float, n_steps: int) -> np.ndarray:
     return np.full(n_steps, float(V), dtype=np.float64)
 
 
+def spike_pair_protocol(dt_pre_post_ms: float, steps_per_ms: int = 2000, t_pre_ms: float = 55.0,
+                        window_ms: float = 120.0, amplitude: float = 1.0,
+                        pulse_ms: float = 1.0) -> np.ndarray:
+    """Spike-timing protocol for the STDP analogue named in the abstract: a
+    +amplitude pulse of pulse_ms at t_pre and a -amplitude pulse at
+    t_post = t_pre + dt_pre_post, summed where they overlap, over a window."""
+    n = int(round(window_ms * steps_per_ms))
+    t = np.arange(n, dtype=np.float64) / steps_per_ms
+    t_post = t_pre_ms + dt_pre_post_ms
+    V = np.zeros(n, dtype=np.float64)
+    V += np.where((t >= t_pre_ms) & (t < t_pre_ms + pulse_ms), amplitude, 0.0)
+    V -= np.where((t >= t_post) & (t < t_post + pulse_ms), amplitude, 0.0)
+    return V
+
+
 # ------------------------------------------------------------ seeded inputs
 
 def random_occupancy(R: int, L: int, fill: float, seed: int) -> np.ndarray:
@@ -133,3 +148,28 @@ def hysteresis_65536x1024(R: int = 65536, L: int = 1024, steps_per_cycle: int = 
     return Workload("hysteresis_%dx%d" % (R, L), dev,
                     triangle_protocol(2.0, steps_per_cycle, cycles),
                     init_mode=1, fill=0.25, Ea_site=Ea)
+
+
+def stdp_batch(n_inst: int = 512, seed: int = 7, n_steps: Optional[int] = None,
+               steps_per_ms: int = 2000):
+    """Batched devices: rails log-uniform in [256, 16,384], sites log-uniform
+    in [128, 2,048], filling U(0.05, 0.4), each with a spike-pair protocol of
+    1 V, 1 ms pulses and pre-post delay U(-50, 50) ms at 2,000 steps per ms.
+    Returns (devices, voltage tables, fills, delays_ms); n_steps truncates the
+    tables (for timing a bounded window)."""
+    rng = np.random.default_rng(seed)
+    devs, Vs, fills, delays = [], [], [], []
+    for i in range(n_inst):
+        R = int(round(np.exp(rng.uniform(np.log(256), np.log(16384)))))
+        L = int(round(np.exp(rng.uniform(np.log(128), np.log(2048)))))
+        fill = float(rng.uniform(0.05, 0.4))
+        d = float(rng.uniform(-50.0, 50.0))
+        V = spike_pair_protocol(d, steps_per_ms)
+        if n_steps is not None:
+            V = V[:n_steps]
+        devs.append(Device(R=R, L=L, Z=10, electrodes=0, dt=1e-3 / steps_per_ms, seed=seed,
+                           instance=i))
+        Vs.append(V)
+        fills.append(fill)
+        delays.append(d)
+    return devs, Vs, fills, delays

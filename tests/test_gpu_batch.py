@@ -89,6 +89,21 @@ def test_batch_autotuner_leaves_the_simulation_unchanged(kmc):
     b.close()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_accept_path_modes_bit_exact(kmc, mode):
+    """Both batch kernels (with and without the inline accept path) on the same
+    mixed batch, against the oracle."""
+    n_steps = 260
+    devs, Vs, occs = _batch_case(8, n_steps, seed=5)
+    b = kmc.Batch(devs, Vs, [2] * len(devs), occ0s=occs)
+    b.set_accept_path(mode)
+    assert b.accept_path == mode
+    b.set_launch(4, 100)
+    b.step_n(n_steps)
+    _check_against_oracle(b, devs, Vs, occs, n_steps)
+    b.close()
+
+
 def test_batch_rejects_mixed_seeds(kmc):
     devs, Vs, occs = _batch_case(2, 10, seed=4)
     devs[1]["seed"] = 78

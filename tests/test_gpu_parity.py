@@ -30,12 +30,15 @@ def _dev(**kw):
     return d
 
 
-def _compare(kmc, dev, V, occ0, Ea=None, chunks=None, warps=0, flush=0):
+def _compare(kmc, dev, V, occ0, Ea=None, chunks=None, warps=0, flush=0, accept=-1):
     """Run GPU and oracle from the same occupancy; compare everything."""
     n = len(V)
     sim = kmc.Sim(dev, V, init_mode=2, occ0=occ0, Ea_site=Ea)
     if warps or flush:
         sim.set_launch(warps, flush)
+    if accept >= 0:
+        sim.set_accept_path(accept)
+        assert sim.accept_path == accept
     orc = oracle.OracleSim(dev, V, occ0, Ea)
     for c in (chunks or [n]):
         sim.step_n(c)
@@ -105,6 +108,23 @@ def test_chunked_steps_and_launch_shapes_identical(kmc):
     for x, y in zip(a[:3], b[:3]):
         assert np.array_equal(x, y)
     for x, y in zip(a[:3], c[:3]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("dt", [1e-9, 5e-7, 5e-6])
+@pytest.mark.parametrize("L,electrodes,per_site", [(100, 0, False), (33, 1, False), (1024, 1, True),
+                                                   (2048, 1, False), (7, 0, True)])
+def test_accept_path_modes_bit_exact(kmc, dt, L, electrodes, per_site):
+    """The kernels with and without the inline accept path, at small and large
+    hop probabilities (P0 from 4e-4 to 0.9), give the oracle's trajectory."""
+    R = 24
+    dev = _dev(R=R, L=L, Z=min(10, L), dt=dt, electrodes=electrodes, k_e=1e6 if electrodes else 0.0,
+               rho_e=0.3 if electrodes else 0.0)
+    occ0 = W.random_occupancy(R, L, 0.3, seed=L + 11)
+    Ea = W.normal_barriers(R, L, 0.40, 0.02, seed=L) if per_site else None
+    V = W.triangle_protocol(3.0, 120, 2)
+    res = [_compare(kmc, dev, V, occ0, Ea=Ea, accept=m) for m in (0, 1)]
+    for x, y in zip(res[0][:3], res[1][:3]):
         assert np.array_equal(x, y)
 
 
