@@ -139,8 +139,8 @@ void orc_p0_table(const orc_params *P, const double *Ea_site, double *P0)
 /* ------------------------------------------------------------------------ */
 /* Space-charge field per zone (S2.1.8) and Eqs. 3-4 plus 1/(1+B).          */
 /* ------------------------------------------------------------------------ */
-void orc_zone_field(const orc_params *P, const int32_t *Nz, int32_t N0, double V,
-                    double *dV, double *B, double *inv)
+/* Enclosed charge of zone z relative to its rail mean, Q_z - Qbar (S2.1.8). */
+static void zone_charge(const orc_params *P, const int32_t *Nz, int32_t N0, double *dq)
 {
     const int L = P->L, Z = P->Z;
     int32_t w[ORC_MAX_ZONES];
@@ -158,11 +158,20 @@ void orc_zone_field(const orc_params *P, const int32_t *Nz, int32_t N0, double V
     double acc = 0.0;
     for (int z = 0; z < Z; ++z) acc = acc + (double)w[z] * Q[z];
     double Qbar = acc / (double)L;
+    for (int z = 0; z < Z; ++z) dq[z] = Q[z] - Qbar;
+}
+
+void orc_zone_field(const orc_params *P, const int32_t *Nz, int32_t N0, double V,
+                    double *dV, double *B, double *inv)
+{
+    const int L = P->L, Z = P->Z;
+    double dq[ORC_MAX_ZONES];
+    zone_charge(P, Nz, N0, dq);
     double ka = P->kappa * P->alpha;
     double kT = ORC_KB * P->T;
     double t_dev = (double)L * P->d;
     for (int z = 0; z < Z; ++z) {
-        dV[z] = V - ka * (Q[z] - Qbar);
+        dV[z] = V - ka * dq[z];
         double dE = (dV[z] * P->d) / t_dev;   /* Eq. 3, q = 1 e */
         B[z] = exp(-dE / kT);                 /* Eq. 4 */
         inv[z] = 1.0 / (1.0 + B[z]);          /* Eqs. 5-6 denominator */
@@ -268,10 +277,71 @@ static int trial(double u, double p, orc_log_entry *log, int64_t cap, int64_t *c
     return u <= p;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Likelihood-ratio score of the trials of one rail-step (not part of the    */
+/* paper's method: the derivative of the log-probability of the trajectory   */
+/* that a likelihood-ratio gradient of an observable needs).  Every trial is  */
+/* a Bernoulli(p) draw, so its outcome a contributes                         */
+/*     a d ln p + (1 - a) d ln(1 - p)  =  (a - p) / (1 - p) * d ln p         */
+/* with, for p = base B^s / (1 + B) (s = 1 right, 0 left, Eqs. 5-6):          */
+/*     d ln p / d kappa = (s - B / (1 + B)) d ln B / d kappa,                */
+/*     d ln B / d kappa = alpha (Q_z - Qbar) d / (t_dev kB T)    (Eqs. 3-4), */
+/* and for an inner hop (base P0 = 1 - exp(-x), x = 2 nu exp(-Ea/kT) dt):     */
+/*     d ln P0 / d Ea = -(x / kT) exp(-x) / P0,                              */
+/*     d ln P0 / d nu = (x / nu) exp(-x) / P0.                               */
+/* Electrode trials do not depend on Ea or nu.  The accumulator also sums   */
+/* the log-probability of the same outcomes under a second parameter set Pe */
+/* (for checking the derivatives by differences).                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const orc_params *Pe;
+    double dlnP0[2];                         /* d ln P0 / d Ea, d ln P0 / d nu at P */
+    double P0e, Ein_e, Eout_e;               /* base probabilities at Pe */
+    double inv[ORC_MAX_ZONES], c[ORC_MAX_ZONES];      /* 1/(1+B), d ln B / d kappa at P */
+    double Be[ORC_MAX_ZONES], inve[ORC_MAX_ZONES];    /* B, 1/(1+B) at Pe */
+    double s[3];                             /* score of the rail-step: Ea, nu, kappa */
+    double ll;                               /* log-probability at Pe */
+    int32_t Nz[ORC_MAX_ZONES];               /* zone counts of the step-start occupancy */
+} orc_trial_acc;
+
+static void acc_begin(orc_trial_acc *a, const orc_params *P, const int32_t *Nz, int32_t N0,
+                      double V, const double *inv)
+{
+    const int Z = P->Z;
+    double dq[ORC_MAX_ZONES], dVe[ORC_MAX_ZONES];
+    zone_charge(P, Nz, N0, dq);
+    const double kT = ORC_KB * P->T;
+    const double t_dev = (double)P->L * P->d;
+    for (int z = 0; z < Z; ++z) {
+        a->inv[z] = inv[z];
+        a->c[z] = (P->alpha * dq[z] * P->d) / (t_dev * kT);
+        a->Nz[z] = Nz[z];
+    }
+    orc_zone_field(a->Pe, Nz, N0, V, dVe, a->Be, a->inve);
+    a->s[0] = a->s[1] = a->s[2] = 0.0;
+    a->ll = 0.0;
+}
+
+static void acc_trial(orc_trial_acc *a, int z, int dir, int kind, double p, int hit)
+{
+    const double w = (p < 1.0) ? ((double)hit - p) / (1.0 - p) : 1.0;
+    const double dk = dir == 0 ? a->inv[z] * a->c[z] : -(1.0 - a->inv[z]) * a->c[z];
+    if (kind == 0) {
+        a->s[0] += w * a->dlnP0[0];
+        a->s[1] += w * a->dlnP0[1];
+    }
+    a->s[2] += w * dk;
+    const double base = kind == 0 ? a->P0e : (kind == 1 ? a->Ein_e : a->Eout_e);
+    double pl, pr;
+    orc_hop_probs(base, a->Be[z], a->inve[z], &pl, &pr);
+    const double pe = dir == 0 ? pr : pl;
+    a->ll += hit ? log(pe) : log1p(-pe);
+}
+
 static void rail_step(const orc_params *P, int r, uint32_t t, double V, uint8_t *occ, int32_t N0,
                       const double *P0row, double P0scalar, double E_in, double E_out,
                       int8_t *mvR, int8_t *mvL, uint8_t *next, int64_t *J_acc, int64_t *zc_acc,
-                      orc_log_entry *log, int64_t cap, int64_t *count)
+                      orc_log_entry *log, int64_t cap, int64_t *count, orc_trial_acc *acc)
 {
     const int L = P->L, Z = P->Z;
     const int open = P->electrodes == 1;
@@ -287,6 +357,7 @@ static void rail_step(const orc_params *P, int r, uint32_t t, double V, uint8_t 
 
     /* field, Eq. 3, Eq. 4 per zone */
     orc_zone_field(P, Nz, N0, V, dV, B, inv);
+    if (acc) acc_begin(acc, P, Nz, N0, V, inv);
 
     /* trials (S2.1.6 - S2.1.7) */
     int injR = 0, injL = 0; /* injection into site 0 / site L-1 */
@@ -313,8 +384,15 @@ static void rail_step(const orc_params *P, int r, uint32_t t, double V, uint8_t 
                 pL = eL;
                 kindL = 2;
             }
-            int aR = okR && trial(uR, pR, log, cap, count, r, t, k, 0, kindR);
-            int aL = okL && trial(uL, pL, log, cap, count, r, t, k, 1, kindL);
+            int aR = 0, aL = 0;
+            if (okR) {
+                aR = trial(uR, pR, log, cap, count, r, t, k, 0, kindR);
+                if (acc) acc_trial(acc, z, 0, kindR, pR, aR);
+            }
+            if (okL) {
+                aL = trial(uL, pL, log, cap, count, r, t, k, 1, kindL);
+                if (acc) acc_trial(acc, z, 1, kindL, pL, aL);
+            }
             /* X + M_right - M_left: both trials succeeding leaves the ion in place */
             if (aR && !aL) mvR[k] = 1;
             if (aL && !aR) mvL[k] = 1;
@@ -322,10 +400,14 @@ static void rail_step(const orc_params *P, int r, uint32_t t, double V, uint8_t 
             double iL, iR;
             orc_hop_probs(E_in, B[z], inv[z], &iL, &iR);
             site_uniforms(P, (uint32_t)k, (uint32_t)r, t, &uR, &uL);
-            if (k == 0) /* a rightward hop from the left reservoir into site 0 */
+            if (k == 0) { /* a rightward hop from the left reservoir into site 0 */
                 injR = trial(uR, iR, log, cap, count, r, t, k, 0, 1);
-            if (k == L - 1) /* a leftward hop from the right reservoir into site L-1 */
+                if (acc) acc_trial(acc, z, 0, 1, iR, injR);
+            }
+            if (k == L - 1) { /* a leftward hop from the right reservoir into site L-1 */
                 injL = trial(uL, iL, log, cap, count, r, t, k, 1, 1);
+                if (acc) acc_trial(acc, z, 1, 1, iL, injL);
+            }
         }
     }
 
@@ -404,7 +486,7 @@ int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, u
                 const int rail = rail_ids ? rail_ids[r] : r;
                 rail_step(P, rail, t, V[t], occ + (int64_t)r * L, N0[r],
                           P0site ? P0site + (int64_t)r * L : NULL, P0scalar, E_in, E_out,
-                          mvR, mvL, next, &Jr, zc, log, log_cap, log_count);
+                          mvR, mvL, next, &Jr, zc, log, log_cap, log_count, NULL);
                 J += Jr;
                 if (J_rail) J_rail[r] += Jr;
             }
@@ -426,4 +508,88 @@ int orc_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Likelihood-ratio gradient of a linear observable of the traces.          */
+/* ------------------------------------------------------------------------ */
+int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64_t t0,
+               int64_t n_steps, uint8_t *occ, const int32_t *N0, const double *wJ,
+               const double *wZ, const int64_t *J_tot, const int64_t *Zc_tot, double *S_cum,
+               double *G, double *loglik, int64_t *J_out, int nthreads)
+{
+    const int R = P->R, L = P->L, Z = P->Z;
+    if (L < 2 || Z < 1 || Z > ORC_MAX_ZONES || Z > L || R < 0) return -1;
+    if (t0 < 0 || t0 + n_steps > (int64_t)ORC_INIT_STEP) return -1;
+    if ((wJ && !J_tot) || (wZ && !Zc_tot)) return -1;
+    const double P0scalar = orc_p0(P->nu, P->Ea, P->T, P->dt);
+    const double E = -expm1(-(2.0 * P->k_e * P->dt));
+    const double E_in = E * P->rho_e;
+    const double E_out = E * (1.0 - P->rho_e);
+    const double kT = ORC_KB * P->T;
+    const double x = 2.0 * orc_gamma0(P->nu, P->Ea, P->T) * P->dt;
+    const double dlnP0_dEa = -((x / kT) * exp(-x)) / P0scalar;
+    const double dlnP0_dnu = ((x / P->nu) * exp(-x)) / P0scalar;
+    const double Ee = -expm1(-(2.0 * Pe->k_e * Pe->dt));
+    const double P0e = orc_p0(Pe->nu, Pe->Ea, Pe->T, Pe->dt);
+    const double loo = R > 1 ? (double)(R - 1) : 0.0;   /* leave-one-out baseline divisor */
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int64_t s = 0; s < n_steps; ++s) {
+        const uint32_t t = (uint32_t)(t0 + s);
+        int64_t J = 0;
+#ifdef _OPENMP
+#pragma omp parallel reduction(+ : J)
+#endif
+        {
+            int8_t *mvR = (int8_t *)malloc((size_t)L);
+            int8_t *mvL = (int8_t *)malloc((size_t)L);
+            uint8_t *next = (uint8_t *)malloc((size_t)L);
+            orc_trial_acc acc;
+            acc.Pe = Pe;
+            acc.dlnP0[0] = dlnP0_dEa;
+            acc.dlnP0[1] = dlnP0_dnu;
+            acc.P0e = P0e;
+            acc.Ein_e = Ee * Pe->rho_e;
+            acc.Eout_e = Ee * (1.0 - Pe->rho_e);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+            for (int r = 0; r < R; ++r) {
+                int64_t Jr = 0;
+                int64_t zc[ORC_MAX_ZONES];
+                for (int z = 0; z < Z; ++z) zc[z] = 0;
+                rail_step(P, r, t, V[t], occ + (int64_t)r * L, N0[r], NULL, P0scalar, E_in, E_out,
+                          mvR, mvL, next, &Jr, zc, NULL, 0, NULL, &acc);
+                double *Sr = S_cum + 4 * (int64_t)r;
+                double *Gr = G + 4 * (int64_t)r;
+                /* zone counts at the start of step t pair with the score of steps < t */
+                if (wZ) {
+                    double fZ = 0.0;
+                    for (int z = 0; z < Z; ++z) {
+                        const double b = loo > 0.0 ? (double)(Zc_tot[s * Z + z] - acc.Nz[z]) / loo : 0.0;
+                        fZ += wZ[s * Z + z] * ((double)acc.Nz[z] - b);
+                    }
+                    for (int i = 0; i < 4; ++i) Gr[i] += fZ * Sr[i];
+                }
+                for (int i = 0; i < 3; ++i) Sr[i] += acc.s[i];
+                /* the current of step t pairs with the score of steps <= t */
+                if (wJ) {
+                    const double b = loo > 0.0 ? (double)(J_tot[s] - Jr) / loo : 0.0;
+                    const double fJ = wJ[s] * ((double)Jr - b);
+                    for (int i = 0; i < 4; ++i) Gr[i] += fJ * Sr[i];
+                }
+                if (loglik) loglik[r] += acc.ll;
+                J += Jr;
+            }
+            free(mvR);
+            free(mvL);
+            free(next);
+        }
+        if (J_out) J_out[s] = J;
+    }
+    return 0;
 }

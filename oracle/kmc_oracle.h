@@ -60,5 +60,23 @@ int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, u
             int64_t *Zc_out, int64_t *J_rail, orc_log_entry *log, int64_t log_cap,
             int64_t *log_count, int nthreads);
 int orc_max_threads(void);
+/* Likelihood-ratio gradient (scalar barrier only) of the observable
+ *     F = sum_s [ wJ[s] J_s + sum_z wZ[s][z] Zc_s[z] ]
+ * over steps t0 .. t0 + n_steps - 1 (s relative to t0), replaying the run from
+ * occ (rails 0 .. R-1, updated in place).  Per rail r it keeps the cumulative
+ * score S_cum[r] = (d/dEa, d/dnu, d/dkappa, d/drho) log-probability of the
+ * rail's trajectory so far (entry 3, the initial-placement score, is set by
+ * the caller and left unchanged), and adds to G[r]
+ *     fZ_s S_cum(before step s) + fJ_s S_cum(after step s),
+ *     fJ_s = wJ[s] (J_rs - (J_tot[s] - J_rs) / (R - 1)),
+ *     fZ_s = sum_z wZ[s][z] (N_rz(s) - (Zc_tot[s][z] - N_rz(s)) / (R - 1)),
+ * with the totals J_tot, Zc_tot of the same run (leave-one-out baselines;
+ * none when R == 1).  The sum of G over rails estimates dE[F]/dtheta without
+ * bias.  loglik[r] (optional) accumulates the log-probability of the same
+ * trial outcomes under parameters Pe.  J_out (optional) receives J_s. */
+int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64_t t0,
+               int64_t n_steps, uint8_t *occ, const int32_t *N0, const double *wJ,
+               const double *wZ, const int64_t *J_tot, const int64_t *Zc_tot, double *S_cum,
+               double *G, double *loglik, int64_t *J_out, int nthreads);
 
 #endif

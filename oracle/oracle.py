@@ -92,6 +92,9 @@ def lib():
                               ctypes.c_int]
         L.orc_run.restype = ctypes.c_int
         L.orc_max_threads.restype = ctypes.c_int
+        L.orc_run_lr.argtypes = [P, P, f64p, ctypes.c_int64, ctypes.c_int64, u8p, i32p, f64p, f64p,
+                                 i64p, i64p, f64p, f64p, f64p, i64p, ctypes.c_int]
+        L.orc_run_lr.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -252,4 +255,61 @@ class OracleSim:
 
 __all__ = ["build", "lib", "philox4x32_10", "zone_of", "zone_widths", "gamma0", "p0",
            "p0_table", "zone_field", "hop_probs", "init_occupancy", "max_threads", "OracleSim", "params",
-           "INIT_STEP", "MAX_ZONES", "LOG_DTYPE"]
+           "INIT_STEP", "MAX_ZONES", "LOG_DTYPE", "init_score_rho", "lr_gradient"]
+
+
+# ------------------------------------------------- likelihood-ratio gradient
+
+def init_score_rho(occ0: np.ndarray, fill: float) -> np.ndarray:
+    """d/drho of the log-probability of each rail's initial Bernoulli(rho)
+    placement: (N0 - L rho) / (rho (1 - rho))."""
+    occ = np.asarray(occ0).reshape(occ0.shape[0], -1)
+    n0 = occ.sum(axis=1).astype(np.float64)
+    L = occ.shape[1]
+    return (n0 - L * fill) / (fill * (1.0 - fill))
+
+
+def lr_gradient(dev, V: np.ndarray, occ0: np.ndarray, n_steps: int,
+                wJ: Optional[np.ndarray] = None, wZ: Optional[np.ndarray] = None,
+                fill: Optional[float] = None, dev_eval=None, nthreads: int = 0) -> dict:
+    """Likelihood-ratio gradient of F = sum_s wJ[s] J_s + sum_{s,z} wZ[s,z] Zc_s[z]
+    over steps 0 .. n_steps-1 of a device started from occ0 (scalar barrier).
+
+    A plain oracle run gives the totals J_s, Zc_s; orc_run_lr then replays the
+    same trajectory and accumulates the per-rail estimator.  The gradient is
+    with respect to (Ea, nu, kappa, rho); the rho entry is NaN unless fill
+    (the Bernoulli filling that produced occ0) is given.  Returns a dict with
+    grad, stderr (from the spread of the independent per-rail terms), G (per
+    rail), S (cumulative score per rail), loglik (per rail, at dev_eval or dev)
+    and J (the replayed totals)."""
+    P = params(dev)
+    Pe = params(dev_eval if dev_eval is not None else dev)
+    occ = np.ascontiguousarray(occ0, dtype=np.uint8).reshape(P.R, P.L).copy()
+    Vc = np.ascontiguousarray(V, dtype=np.float64)
+    fwd = OracleSim(dev, Vc, occ, nthreads=nthreads)
+    J_tot, Zc_tot = fwd.step_n(n_steps)
+    N0 = occ.sum(axis=1).astype(np.int32)
+    S = np.zeros((P.R, 4))
+    if fill is not None:
+        S[:, 3] = init_score_rho(occ, fill)
+    G = np.zeros((P.R, 4))
+    ll = np.zeros(P.R)
+    J = np.zeros(n_steps, dtype=np.int64)
+    wJc = None if wJ is None else np.ascontiguousarray(wJ, dtype=np.float64)
+    wZc = None if wZ is None else np.ascontiguousarray(wZ, dtype=np.float64).reshape(n_steps, P.Z)
+    rc = lib().orc_run_lr(ctypes.byref(P), ctypes.byref(Pe), _ptr(Vc, ctypes.c_double), 0,
+                          n_steps, _ptr(occ, ctypes.c_uint8), _ptr(N0, ctypes.c_int32),
+                          _ptr(wJc, ctypes.c_double), _ptr(wZc, ctypes.c_double),
+                          _ptr(J_tot, ctypes.c_int64), _ptr(Zc_tot, ctypes.c_int64),
+                          _ptr(S, ctypes.c_double), _ptr(G, ctypes.c_double),
+                          _ptr(ll, ctypes.c_double), _ptr(J, ctypes.c_int64), nthreads)
+    if rc != 0:
+        raise ValueError("orc_run_lr failed (%d)" % rc)
+    grad = G.sum(axis=0)
+    R = P.R
+    stderr = np.sqrt(R / max(R - 1, 1) * ((G - G.mean(axis=0)) ** 2).sum(axis=0))
+    if fill is None:
+        grad[3] = np.nan
+        stderr[3] = np.nan
+    return {"grad": grad, "stderr": stderr, "G": G, "S": S, "loglik": ll, "J": J,
+            "J_tot": J_tot, "Zc_tot": Zc_tot}

@@ -47,10 +47,12 @@ def field_B(occ_bits, L, Z, N0, V, dev):
     return B, zones
 
 
-def transition_matrix(dev, V, N0, Ea_site=None):
+def transition_matrix(dev, V, N0, Ea_site=None, with_current=False):
     """Exact one-step transition matrix over all 2^L configurations
     (bit k of the state index = site k occupied).  ``Ea_site`` gives a
-    barrier per site for hops leaving that site (else the scalar Ea)."""
+    barrier per site for hops leaving that site (else the scalar Ea).  With
+    ``with_current`` also the expected net leftward crossings of one step from
+    each configuration (electrode bonds included)."""
     L, Z = dev["L"], dev["Z"]
     open_ = dev["electrodes"] == 1
     kT = KB * dev["T"]
@@ -63,6 +65,7 @@ def transition_matrix(dev, V, N0, Ea_site=None):
     E_in, E_out = E * dev["rho_e"], E * (1.0 - dev["rho_e"])
     n = 1 << L
     T = np.zeros((n, n))
+    Jmean = np.zeros(n)
     for s in range(n):
         occ = [(s >> k) & 1 for k in range(L)]
         B, zones = field_B(occ, L, Z, N0, V, dev)
@@ -115,6 +118,9 @@ def transition_matrix(dev, V, N0, Ea_site=None):
                     nxt[src + d] = 1
             s2 = sum(b << k for k, b in enumerate(nxt))
             T[s, s2] += prob
+            Jmean[s] += prob * sum(-d for d in moves.values())
+    if with_current:
+        return T, Jmean
     return T
 
 
