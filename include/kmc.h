@@ -142,6 +142,39 @@ int kmc_set_launch(kmc_handle *h, int warps_per_cta, int flush_steps);
 int kmc_set_accept_path(kmc_handle *h, int mode);
 int kmc_accept_path(const kmc_handle *h);
 
+/* Likelihood-ratio gradient of an observable's expectation.  The paper's
+ * method has no derivative; this is the score-function (likelihood-ratio)
+ * estimator over the same stochastic dynamics (Eqs. 1, 3-6 give every trial's
+ * probability p, S2.1.6-S2.1.7 its Bernoulli outcome a).  For the steps
+ * 0 .. t-1 simulated so far (t = kmc_current_step) and the observable
+ *     F = sum_s dLoss_dJ[s] J_s + sum_{s,z} dLoss_dZc[s][z] Zc_s[z]
+ * (J, Zc as kmc_observables returns them), grad_out receives an unbiased
+ * estimate of dE[F]/d(Ea_eV, nu_Hz, kappa, fill):
+ *     sum over rails r, steps s of  f_rs * S_r(s),
+ * where S_r(s) is the score of rail r's trajectory up to step s (the sum over
+ * its performed trials of (a - p)/(1 - p) d ln p, plus d/dfill of the
+ * Bernoulli placement) and f_rs is the rail's share of F's step-s term minus
+ * the mean share of the other rails (a baseline that leaves the estimate
+ * unbiased).  Zone counts, recorded at the start of step s, pair with the
+ * score of steps < s; the current of step s with that of steps <= s.
+ * stderr_out (may be NULL) receives the standard error of each entry from the
+ * spread of the independent per-rail terms.
+ *
+ * The backward pass replays the trajectory from the initial occupancy kept at
+ * kmc_create (the Philox counters (site, rail, step, instance) are the only
+ * other checkpoint) with every trial's outcome recomputed, and accumulates the
+ * estimator in FP64 on the device; the forward state is not touched.
+ *  dLoss_dJ    host double [t] or NULL;  dLoss_dZc  host double [t][Z] or NULL.
+ * The fill entry is NaN unless the placement was Bernoulli(fill) (init_mode 1).
+ * The Ea and nu entries refer to the scalar barrier: handles created with
+ * per-site barriers are rejected (KMC_E_ARG).  Electrode exchange enters only
+ * through kappa (rho_electrode and k_electrode_Hz are held fixed).  The first
+ * call allocates the pass's buffers (an occupancy, R x 5 doubles, and weight
+ * tables of n_steps_total entries).  Synchronizes the stream.
+ * Errors: KMC_E_ARG, KMC_E_NOMEM, KMC_E_CUDA. */
+int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, double grad_out[4],
+             double stderr_out[4]);
+
 /* Current absolute step of the handle. */
 int64_t kmc_current_step(const kmc_handle *h);
 

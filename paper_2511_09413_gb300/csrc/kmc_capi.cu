@@ -268,7 +268,8 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
     h->log = (kmc_log_entry *)h->alloc(sizeof(kmc_log_entry) * (size_t)h->log_cap);
     h->misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
     h->args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
-    if (!h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
+    h->occ_init = (uint8_t *)h->alloc(occ_bytes);
+    if (!h->occ_init || !h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
         return fail(KMC_E_NOMEM, "device allocation failed");
     if (Ea) {
         h->P0site = (double *)h->alloc(sizeof(double) * (size_t)(R * L));
@@ -301,6 +302,7 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
     }
     unsigned long long *bad = h->misc + 5;
     CK(setup_row_counts(h->occ, h->stride, (int32_t)R, (int32_t)L, h->N0, bad, s), "row counts");
+    CK(cudaMemcpyAsync(h->occ_init, h->occ, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
 
     int *p0bad = (int *)(h->misc + 6);
     if (Ea) {
@@ -473,6 +475,113 @@ int kmc_set_launch(kmc_handle *h, int warps_per_cta, int flush_steps)
     h->warps_req = warps_per_cta;
     h->flush_req = flush_steps;
     return pick_launch(h);
+}
+
+int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, double grad_out[4],
+             double stderr_out[4])
+{
+    if (!h || !grad_out) return fail(KMC_E_ARG, "handle or grad_out is NULL");
+    if (h->P0site)
+        return fail(KMC_E_ARG, "kmc_grad needs a scalar barrier (the handle has per-site Ea)");
+    const kmc_params &p = h->p;
+    const int64_t R = p.n_rails, L = p.n_sites, Z = p.n_zones, n = h->t;
+    const bool has_rho = p.init_mode == 1 && p.fill > 0.0 && p.fill < 1.0;
+    double out[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    cudaStream_t s = h->stream;
+    if (n > 0 && (dLoss_dJ || dLoss_dZc)) {
+        const size_t occ_bytes = (size_t)(R * h->stride);
+        const size_t nt = (size_t)std::max<int64_t>(h->n_total, 1);
+        if (!h->g_occ) {
+            h->g_occ = (uint8_t *)h->alloc(occ_bytes);
+            h->g_state = (double *)h->alloc(sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1));
+            h->g_wJ = (double *)h->alloc(sizeof(double) * nt);
+            h->g_wZ = (double *)h->alloc(sizeof(double) * nt * (size_t)Z);
+            h->g_out = (double *)h->alloc(sizeof(double) * 8);
+            h->g_misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
+            h->g_args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
+            if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_wZ || !h->g_out || !h->g_misc ||
+                !h->g_args_dev)
+                return fail(KMC_E_NOMEM, "device allocation failed (gradient pass)");
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (dLoss_dJ && !isfinite(dLoss_dJ[i]))
+                return fail(KMC_E_ARG, "dLoss_dJ[%lld] is not finite", (long long)i);
+        if (dLoss_dZc)
+            for (int64_t i = 0; i < n * Z; ++i)
+                if (!isfinite(dLoss_dZc[i]))
+                    return fail(KMC_E_ARG, "dLoss_dZc[%lld] is not finite", (long long)i);
+        if (dLoss_dJ)
+            CK(cudaMemcpyAsync(h->g_wJ, dLoss_dJ, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s),
+               "copy dLoss_dJ");
+        if (dLoss_dZc)
+            CK(cudaMemcpyAsync(h->g_wZ, dLoss_dZc, sizeof(double) * (size_t)(n * Z),
+                               cudaMemcpyHostToDevice, s),
+               "copy dLoss_dZc");
+        CK(cudaMemcpyAsync(h->g_occ, h->occ_init, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
+        CK(cudaMemsetAsync(h->g_state, 0, sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1), s),
+           "memset");
+        CK(cudaMemsetAsync(h->g_misc, 0, sizeof(unsigned long long) * 8, s), "memset");
+        // the replay: same trajectory (same counters), no traces, no log
+        SweepArgs ga = h->args;
+        ga.occ = h->g_occ;
+        ga.self = h->g_args_dev;
+        ga.J = nullptr;
+        ga.Zc = nullptr;
+        ga.log = h->log;
+        ga.log_cap = 0;
+        ga.log_count = h->g_misc;
+        ga.counters = h->g_misc + 1;
+        ga.wJ = dLoss_dJ ? h->g_wJ : nullptr;
+        ga.wZ = dLoss_dZc ? h->g_wZ : nullptr;
+        ga.J_tot = h->J;
+        ga.Zc_tot = h->Zc;
+        ga.gstate = h->g_state;
+        ga.loo = R > 1 ? (double)(R - 1) : 0.0;
+        ga.alpha = p.alpha_V;
+        const double kT = 8.6173e-5 * p.T_K;
+        ga.tdev_kT = ((double)L * p.site_spacing_nm) * kT;
+        CK(cudaMemcpyAsync(h->g_args_dev, &ga, sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
+           "copy args");
+        SweepLaunch l = h->launch;
+        int dev = 0, max_smem = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (max_smem <= 0) max_smem = 48 * 1024;
+        max_smem = std::min(max_smem, 200 * 1024);
+        int warps = 8;
+        while (warps > 1 && grad_smem_bytes(l.lpr, l.wpl, (int)Z, (int)L, warps) > (size_t)max_smem)
+            warps >>= 1;
+        if (grad_smem_bytes(l.lpr, l.wpl, (int)Z, (int)L, warps) > (size_t)max_smem)
+            return fail(KMC_E_ARG, "gradient pass: shared memory exceeds the device limit");
+        l.warps = warps;
+        l.smem = grad_smem_bytes(l.lpr, l.wpl, (int)Z, (int)L, warps);
+        const int64_t rails_per_cta = (int64_t)(32 / l.lpr) * warps;
+        l.grid = (int)((R + rails_per_cta - 1) / rails_per_cta);
+        for (int64_t t0 = 0; t0 < n; t0 += (int64_t)1 << 30) {
+            ga.t0 = t0;
+            ga.n_steps = (int32_t)std::min<int64_t>(n - t0, (int64_t)1 << 30);
+            ga.flush = ga.n_steps;
+            CK(grad_launch(ga, l, s), "gradient pass launch");
+        }
+        // d ln P0 / d Ea and d ln P0 / d nu (Eq. 1, P0 = 1 - exp(-x), x = 2 Gamma0 dt)
+        const double x = 2.0 * (p.nu_Hz * exp(-p.Ea_eV / kT)) * p.dt_s;
+        const double P0 = -expm1(-x);
+        const double cEa = -((x / kT) * exp(-x)) / P0;
+        const double cnu = ((x / p.nu_Hz) * exp(-x)) / P0;
+        CK(grad_reduce(h->g_state, R, h->N0, (int)L, p.fill, has_rho ? 1 : 0, cEa, cnu, h->g_out, s),
+           "gradient reduce launch");
+        CK(cudaMemcpyAsync(out, h->g_out, sizeof(out), cudaMemcpyDeviceToHost, s), "copy gradient");
+        CK(cudaStreamSynchronize(s), "gradient pass");
+    }
+    for (int i = 0; i < 4; ++i) {
+        grad_out[i] = out[i];
+        if (stderr_out) stderr_out[i] = out[4 + i];
+    }
+    if (!has_rho) {
+        grad_out[3] = NAN;
+        if (stderr_out) stderr_out[3] = NAN;
+    }
+    return KMC_OK;
 }
 
 int kmc_set_accept_path(kmc_handle *h, int mode)

@@ -43,6 +43,15 @@ struct kmc_handle {
     unsigned long long *misc = nullptr;  // [0] log count, [1..3] counters, [4] scratch count
     kmc::SweepArgs *args_dev = nullptr;       // device copy of args for the kernels' rare paths
     int64_t log_cap = 4096;
+    uint8_t *occ_init = nullptr;              // occupancy at step 0: the gradient pass's checkpoint
+
+    // gradient pass (allocated at the first kmc_grad)
+    uint8_t *g_occ = nullptr;                 // replayed occupancy
+    double *g_state = nullptr;                // [R][kGradState]
+    double *g_wJ = nullptr, *g_wZ = nullptr;  // observable weights per step
+    double *g_out = nullptr;                  // [8] sums and standard errors
+    unsigned long long *g_misc = nullptr;     // log count and counters of the replay
+    kmc::SweepArgs *g_args_dev = nullptr;
 
     kmc::SweepArgs args{};
     kmc::SweepLaunch launch{};

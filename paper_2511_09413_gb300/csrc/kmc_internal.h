@@ -62,7 +62,23 @@ struct SweepArgs {
     float delta;                  // relative half-width of the FP32 probability band
     float P0f_scalar;             // scalar P0 in FP32 (host copy of DevConst::P0f)
     float E_inf, E_outf;          // electrode base probabilities in FP32
+
+    // likelihood-ratio gradient pass only (unused by the forward sweep)
+    const double *wJ;                    // [n_steps_total] weight of J_t in the observable
+    const double *wZ;                    // [n_steps_total][Z] weight of Zc_t[z], or null
+    const unsigned long long *J_tot;     // [n_steps_total] the forward's J_t
+    const unsigned long long *Zc_tot;    // [n_steps_total][Z] the forward's Zc_t
+    double *gstate;                      // [R][kGradState] per-rail accumulators
+    double loo;                          // R - 1 (leave-one-out divisor), 0 when R == 1
+    double alpha;                        // space-charge volts per excess ion
+    double tdev_kT;                      // t_dev kB T (d ln B / d kappa denominator)
 };
+
+// Per-rail state of the gradient pass: cumulative inner-trial weight W (the
+// Ea and nu scores are W times d ln P0 / d theta), cumulative kappa score K,
+// and the estimator sums G_W, G_K, G_1 (the rho term is G_1 times the rail's
+// initial-placement score).
+constexpr int kGradState = 5;
 
 // One work item of a batched launch: a tile of rails of one device.
 struct BatchItem {
@@ -104,6 +120,11 @@ size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bo
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
+// gradient pass: shared memory of a launch, the launch, and the final sum
+size_t grad_smem_bytes(int lpr, int wpl, int Z, int L, int warps);
+cudaError_t grad_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
+cudaError_t grad_reduce(const double *gstate, int64_t R, const int32_t *N0, int L, double fill,
+                        int has_rho, double cEa, double cnu, double *out, cudaStream_t s);
 int sweep_kind(int lpr, int wpl);
 cudaError_t batch_set_smem_limit();
 // launches the batched sweep and then advances *t0 by n_steps and re-arms work

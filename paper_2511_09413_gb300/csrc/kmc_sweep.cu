@@ -137,6 +137,13 @@ struct Layout {
         return FIXED + rm_bytes(Z, acc) + 2 * gz8(Z) + pb_bytes(Z) +
                (persite ? align16((size_t)4 * 1024 * WPL) : 0);
     }
+    // gradient pass, appended: accepted-trial masks accR, accL uint32 [W] each,
+    // Q_z double [G][Z] (gzq = align16(8 G Z) bytes), (W_z, K_z) double2 [G][Z]
+    // (2 gzq bytes), per-rail state double [G][8]
+    __host__ __device__ static size_t grad_bytes(int Z)
+    {
+        return 2 * align16(4 * W) + 3 * align16((size_t)8 * G * Z) + align16((size_t)64 * G);
+    }
 };
 
 template <int LPR, int WPL>
@@ -146,6 +153,8 @@ struct WarpSmem {
     uint32_t rz;    // Layout::rm_bytes(Z, acc)
     uint32_t gz;    // Layout::gz8(Z)
     uint32_t pbz;   // Layout::pb_bytes(Z)
+    uint32_t goff;  // Layout::bytes(Z, persite, acc): start of the gradient-pass region
+    uint32_t gzq;   // align16(8 G Z)
     __device__ uint32_t *mvR() const { return (uint32_t *)(b + Ly::MVR); }
     __device__ uint32_t *mvL() const { return (uint32_t *)(b + Ly::MVL); }
     __device__ uint32_t *fR() const { return (uint32_t *)(b + Ly::FR); }
@@ -166,6 +175,17 @@ struct WarpSmem {
     __device__ float2 *P0b() const { return (float2 *)(b + Ly::FIXED + rz + gz); }
     __device__ int32_t *Pb() const { return (int32_t *)(b + Ly::FIXED + rz + 2 * gz); }
     __device__ float *P0f() const { return (float *)(b + Ly::FIXED + rz + 2 * gz + pbz); }
+    __device__ uint32_t *accR() const { return (uint32_t *)(b + goff); }
+    __device__ uint32_t *accL() const { return (uint32_t *)(b + goff + align16(4 * Ly::W)); }
+    __device__ double *gQ() const { return (double *)(b + goff + 2 * align16(4 * Ly::W)); }
+    __device__ double2 *gWK() const
+    {
+        return (double2 *)(b + goff + 2 * align16(4 * Ly::W) + gzq);
+    }
+    __device__ double *gS() const
+    {
+        return (double *)(b + goff + 2 * align16(4 * Ly::W) + 3 * gzq);
+    }
 };
 
 // --------------------------------------------------------- exact FP64 path
@@ -286,10 +306,15 @@ __device__ __forceinline__ Decision decide(const WarpSmem<LPR, WPL> &S, const Sw
 }
 
 // Record an accepted net move (both trials accepted: the ion stays, S2.1.7).
-template <int LPR, int WPL>
+// The gradient pass also marks every accepted trial.
+template <int LPR, int WPL, bool GRAD = false>
 __device__ __forceinline__ bool record_move(const WarpSmem<LPR, WPL> &S, const Decision &D, int g2)
 {
     constexpr int G = 32 / LPR;
+    if constexpr (GRAD) {
+        if (D.dR == 1) atomicOr(&S.accR()[D.idx], D.bit);
+        if (D.dL == 1) atomicOr(&S.accL()[D.idx], D.bit);
+    }
     if (D.dR == 1 && D.dL != 1) {
         if (!D.occd) S.inj()[g2] = 1;               // injection into site 0
         else atomicOr(&S.mvR()[D.idx], D.bit);
@@ -310,7 +335,7 @@ __device__ __forceinline__ bool record_move(const WarpSmem<LPR, WPL> &S, const D
 // in FP64 with the oracle's operation order (exact_zone) and comparing u <= p.
 // Reads the launch arguments through their copy in global memory (g), which
 // keeps the parameter block in the constant bank for the draw loop.
-template <int LPR, int WPL>
+template <int LPR, int WPL, bool GRAD = false>
 __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const SweepArgs *g, int i,
                                             int n_inner, int64_t rail0, uint32_t t,
                                             const uint8_t *zone_tab, bool persite, float flo,
@@ -333,7 +358,7 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
             if (slot < kDeferCap) S.def()[slot] = (uint16_t)i;
             return false;
         }
-        return record_move<LPR, WPL>(S, D, g2);
+        return record_move<LPR, WPL, GRAD>(S, D, g2);
     }
     if (!undecided) return false;   // decided (and applied) in the draw loop
     const DevConst *K = g->K;
@@ -357,10 +382,120 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
         ++ne;
     }
     atomicAdd(&g->counters[1], (unsigned long long)ne);
-    return record_move<LPR, WPL>(S, D, g2);
+    return record_move<LPR, WPL, GRAD>(S, D, g2);
 }
 
-template <int LPR, int WPL, bool ACC>
+// ------------------------------------------------- likelihood-ratio score
+// Summed score weight of n Bernoulli(p) trials of which A succeeded: each
+// trial contributes (a - p) / (1 - p) times d ln p (a certain trial, p >= 1,
+// contributes d ln p).
+__device__ __forceinline__ double trial_weight(int A, int n, double p)
+{
+    if (n == 0) return 0.0;
+    if (p >= 1.0) return (double)A;
+    return __ddiv_rn(__dsub_rn((double)A, __dmul_rn((double)n, p)), __dsub_rn(1.0, p));
+}
+
+// Score of one step for the rails of a warp (gradient pass).  Trials are
+// grouped per (rail, zone): inner hops of a zone share p (scalar barrier), so
+// their summed weight needs only the counts of performed and accepted trials
+// from the step-start masks ow, fR, fL and the accepted-trial masks; the
+// electrode trials of the two boundary sites are added one by one.  Writes
+// (W_z, K_z) per (rail, zone): the summed inner-trial weight (times
+// d ln P0 / d theta it is the Ea and nu score) and the kappa score with
+// d ln p / d kappa = (s - B/(1+B)) d ln B / d kappa, s = 1 right, 0 left.
+template <int LPR, int WPL>
+__device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSmem<LPR, WPL> &S,
+                                                uint32_t t, int nact, bool open, int lane)
+{
+    constexpr int G = 32 / LPR;
+    const int L = a.L, Z = a.Z;
+    const DevConst &K = *a.K;
+    const double V = a.V[t];
+    // enclosed charge Q_z and its rail mean, one lane per rail, oracle order
+    if (lane % LPR == 0 && lane / LPR < nact) {
+        const int g = lane / LPR;
+        const int32_t *Pb = S.Pb() + g * (Z + 1);
+        const double Ld = (double)L;
+        const int32_t n0 = S.N0s()[g];
+        double run = 0.0, acc = 0.0;
+        for (int z = 0; z < Z; ++z) {
+            const int w = K.bnd[z + 1] - K.bnd[z];
+            const int Nz = Pb[z + 1] - Pb[z];
+            const double C = __dsub_rn((double)Nz, __ddiv_rn(__dmul_rn((double)n0, (double)w), Ld));
+            const double Q = __dadd_rn(run, __dmul_rn(0.5, C));
+            run = __dadd_rn(run, C);
+            acc = __dadd_rn(acc, __dmul_rn((double)w, Q));
+            S.gQ()[g * Z + z] = Q;
+        }
+        S.gS()[g * 8 + 5] = __ddiv_rn(acc, Ld);
+    }
+    __syncwarp();
+    for (int pi = lane; pi < G * Z; pi += 32) {
+        const int g = pi / Z, z = pi - g * Z;
+        if (g >= nact) continue;
+        // Eqs. 3-6 in the oracle's operation order
+        const double dq = __dsub_rn(S.gQ()[pi], S.gS()[g * 8 + 5]);
+        const double dV = __dsub_rn(V, __dmul_rn(K.ka, dq));
+        const double dE = __ddiv_rn(__dmul_rn(dV, K.d), K.t_dev);
+        const double B = exp(__ddiv_rn(-dE, K.kT));
+        const double inv = __ddiv_rn(1.0, __dadd_rn(1.0, B));
+        const double pL = __dmul_rn(K.P0, inv);
+        const double pR = __dmul_rn(pL, B);
+        const double c = __ddiv_rn(__dmul_rn(__dmul_rn(a.alpha, dq), K.d), a.tdev_kT);
+        const double dkR = __dmul_rn(inv, c);
+        const double dkL = -__dmul_rn(__dsub_rn(1.0, inv), c);
+        // inner trials of the zone's sites [lo, hi); at an open rail the outward
+        // trials of sites 0 and L-1 are electrode trials, counted below
+        const int lo = K.bnd[z], hi = K.bnd[z + 1];
+        int nR = 0, nL = 0, aR = 0, aL = 0;
+        for (int w = lo >> 5; w <= (hi - 1) >> 5; ++w) {
+            const int s0 = 32 * w;
+            uint32_t m = FULL;
+            if (lo > s0) m &= FULL << (lo - s0);
+            if (hi < s0 + 32) m &= (1u << (hi - s0)) - 1u;
+            const int idx = g * LPR * WPL + w;
+            const uint32_t o = S.ow()[idx] & m;
+            uint32_t fR = S.fR()[idx], fL = S.fL()[idx];
+            if (open) {
+                if (L - 1 >= s0 && L - 1 < s0 + 32) fR &= ~(1u << ((L - 1) - s0));
+                if (s0 == 0) fL &= ~1u;
+            }
+            nR += __popc(o & fR);
+            nL += __popc(o & fL);
+            aR += __popc(o & fR & S.accR()[idx]);
+            aL += __popc(o & fL & S.accL()[idx]);
+        }
+        const double wR = trial_weight(aR, nR, pR), wL = trial_weight(aL, nL, pL);
+        const double Wz = __dadd_rn(wR, wL);
+        double Kz = __dadd_rn(__dmul_rn(wR, dkR), __dmul_rn(wL, dkL));
+        if (open && z == 0) {
+            const int idx = g * LPR * WPL;
+            if (S.ow()[idx] & 1u) {        // extraction through the left electrode
+                const double pe = __dmul_rn(K.E_out, inv);
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accL()[idx] & 1u) ? 1 : 0, 1, pe), dkL));
+            } else {                       // injection into site 0
+                const double pe = __dmul_rn(__dmul_rn(K.E_in, inv), B);
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accR()[idx] & 1u) ? 1 : 0, 1, pe), dkR));
+            }
+        }
+        if (open && z == Z - 1) {
+            const int idx = g * LPR * WPL + ((L - 1) >> 5);
+            const uint32_t bit = 1u << ((L - 1) & 31);
+            if (S.ow()[idx] & bit) {       // extraction through the right electrode
+                const double pe = __dmul_rn(__dmul_rn(K.E_out, inv), B);
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accR()[idx] & bit) ? 1 : 0, 1, pe), dkR));
+            } else {                       // injection into site L-1
+                const double pe = __dmul_rn(K.E_in, inv);
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accL()[idx] & bit) ? 1 : 0, 1, pe), dkL));
+            }
+        }
+        S.gWK()[pi] = make_double2(Wz, Kz);
+    }
+    __syncwarp();
+}
+
+template <int LPR, int WPL, bool ACC, bool GRAD = false>
 // One CTA's tile of rails advanced through steps [t0, t0 + n_steps): the whole
 // sweep of S2.1.2 - S2.1.7 for rails [tile_rail0, tile_rail0 + G * warps).
 // `a` describes one device (in the kernel's parameter space for a single
@@ -392,14 +527,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     const int nact = (int)max((int64_t)0, min((int64_t)G, (int64_t)a.R - rail0));
 
     using Ly = Layout<LPR, WPL>;
-    const size_t wb = Ly::bytes(Z, persite, ACC);
+    const size_t wb0 = Ly::bytes(Z, persite, ACC);
+    const size_t wb = wb0 + (GRAD ? Ly::grad_bytes(Z) : 0);
     WarpSmem<LPR, WPL> S;
     S.b = smem + (size_t)warp * wb;
     S.rz = (uint32_t)Ly::rm_bytes(Z, ACC);
     S.gz = (uint32_t)Ly::gz8(Z);
     S.pbz = (uint32_t)Ly::pb_bytes(Z);
+    S.goff = (uint32_t)wb0;
+    S.gzq = (uint32_t)align16((size_t)8 * G * Z);
+    // the gradient pass writes no traces: no trace buffer
+    const int trace_len = GRAD ? 0 : flush * (1 + Z);
     int32_t *trace = (int32_t *)(smem + (size_t)nwarps * wb);
-    uint8_t *zone_tab = (uint8_t *)(trace + (size_t)flush * (1 + Z));
+    uint8_t *zone_tab = (uint8_t *)(trace + trace_len);
 
     // ---- per-CTA tables and per-warp staging
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -407,10 +547,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         while (a.bnd[z + 1] <= k) ++z;
         zone_tab[k] = (uint8_t)z;
     }
-    for (int i = threadIdx.x; i < flush * (1 + Z); i += blockDim.x) trace[i] = 0;
+    for (int i = threadIdx.x; i < trace_len; i += blockDim.x) trace[i] = 0;
     for (int i = lane; i < 32 * WPL; i += 32) {
         S.mvR()[i] = 0;
         S.mvL()[i] = 0;
+        if constexpr (GRAD) {
+            S.accR()[i] = 0;
+            S.accL()[i] = 0;
+        }
+    }
+    if constexpr (GRAD) {
+        if (sl == 0)
+            for (int i = 0; i < kGradState; ++i)
+                S.gS()[seg * 8 + i] = active ? a.gstate[rail * kGradState + i] : 0.0;
     }
     for (int i = lane; i < 2 * G; i += 32) S.inj()[i] = 0;
     if (sl == 0) S.N0s()[seg] = active ? a.N0[rail] : 0;
@@ -661,11 +810,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             }
 
             // ---- zone counts of the step-start occupancy into the trace
-            for (int pi = lane; pi < G * Z; pi += 32) {
-                const int g2 = pi / Z;
-                const int z = pi - g2 * Z;
-                const int nz = S.Pb()[g2 * (Z + 1) + z + 1] - S.Pb()[g2 * (Z + 1) + z];
-                if (nz != 0) atomicAdd(&tr[1 + z], nz);
+            if constexpr (!GRAD) {
+                for (int pi = lane; pi < G * Z; pi += 32) {
+                    const int g2 = pi / Z;
+                    const int z = pi - g2 * Z;
+                    const int nz = S.Pb()[g2 * (Z + 1) + z + 1] - S.Pb()[g2 * (Z + 1) + z];
+                    if (nz != 0) atomicAdd(&tr[1 + z], nz);
+                }
             }
             if (lane == 0) {
                 S.ndef()[0] = 0;
@@ -712,6 +863,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                             const bool tL = (S.fL()[idx] & bit) != 0;
                             const int dR = tR ? (xy[q] < th[q].z ? 1 : (xy[q] > th[q].x ? 0 : 2)) : 0;
                             const int dL = tL ? (xw[q] < th[q].w ? 1 : (xw[q] > th[q].y ? 0 : 2)) : 0;
+                            if constexpr (GRAD) {
+                                if (dR != 2 && dL != 2) {
+                                    if (dR == 1) atomicOr(&S.accR()[idx], bit);
+                                    if (dL == 1) atomicOr(&S.accL()[idx], bit);
+                                }
+                            }
                             if (dR == 2 || dL == 2) {
                                 slow = true;        // per-site refinement or the exact pass
                             } else if (dR == 1 && dL != 1) {
@@ -723,7 +880,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                             }                       // both accepted: the ion stays
                         }
                         if (slow)
-                            moved |= slow_candidate<LPR, WPL>(S, a.self, i, n_inner, rail0, t,
+                            moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i, n_inner, rail0, t,
                                                               zone_tab, persite, flo, fhi, false,
                                                               xy[q], xw[q]);
                     }
@@ -754,7 +911,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     #pragma unroll
                     for (int q = 0; q < kDrawIlp; ++q)
                         if (at[q])
-                            moved |= slow_candidate<LPR, WPL>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
+                            moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
                                                               zone_tab, persite, flo, fhi, false, xy[q],
                                                               xw[q]);
                 }
@@ -768,12 +925,48 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 const int cnt2 = overflow ? nlist : nd;
                 for (int k = lane; k < cnt2; k += 32) {
                     const int i = overflow ? k : (int)S.def()[k];
-                    moved |= slow_candidate<LPR, WPL>(S, a.self, i, n_inner, rail0, t, zone_tab,
+                    moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i, n_inner, rail0, t, zone_tab,
                                                       persite, flo, fhi, true, 0u, 0u);
                 }
             }
 
+            // ---- 5c. gradient pass: score of this step's trials
+            if constexpr (GRAD) {
+                __syncwarp();
+                grad_step_score<LPR, WPL>(a, S, t, nact, open, lane);
+                if (sl == 0 && seg < nact) {
+                    double *st = S.gS() + seg * 8;       // W, K, G_W, G_K, G_1
+                    double Ws = 0.0, Ks = 0.0;
+                    for (int z = 0; z < Z; ++z) {
+                        const double2 wk = S.gWK()[seg * Z + z];
+                        Ws = __dadd_rn(Ws, wk.x);
+                        Ks = __dadd_rn(Ks, wk.y);
+                    }
+                    if (a.wZ) {
+                        // zone counts at the start of step t pair with the score of steps < t
+                        double fZ = 0.0;
+                        for (int z = 0; z < Z; ++z) {
+                            const int nz = S.Pb()[seg * (Z + 1) + z + 1] - S.Pb()[seg * (Z + 1) + z];
+                            const long long tot = (long long)a.Zc_tot[(int64_t)t * Z + z];
+                            const double b = a.loo > 0.0 ? __ddiv_rn((double)(tot - nz), a.loo) : 0.0;
+                            fZ = __dadd_rn(fZ, __dmul_rn(a.wZ[(int64_t)t * Z + z], __dsub_rn((double)nz, b)));
+                        }
+                        st[2] = __dadd_rn(st[2], __dmul_rn(fZ, st[0]));
+                        st[3] = __dadd_rn(st[3], __dmul_rn(fZ, st[1]));
+                        st[4] = __dadd_rn(st[4], fZ);
+                    }
+                    st[0] = __dadd_rn(st[0], Ws);
+                    st[1] = __dadd_rn(st[1], Ks);
+                }
+#pragma unroll
+                for (int j = 0; j < WPL; ++j) {
+                    S.accR()[seg * LPR * WPL + wbase + j] = 0u;
+                    S.accL()[seg * LPR * WPL + wbase + j] = 0u;
+                }
+            }
+
             // ---- 6. conflicts, synchronous update, current
+            int Jrail = 0;   // this rail's J_t (gradient pass)
             dirty = __any_sync(FULL, moved);
             if (dirty) {
                 __syncwarp();
@@ -832,12 +1025,33 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     S.inj()[seg] = 0;
                     S.inj()[G + seg] = 0;
                 }
-                const int Jw = __reduce_add_sync(FULL, Jl);
-                if (lane == 0 && Jw != 0) atomicAdd(&tr[0], Jw);
+                if constexpr (GRAD) {
+                    int v = Jl;
+#pragma unroll
+                    for (int off2 = LPR / 2; off2 >= 1; off2 >>= 1)
+                        v += __shfl_xor_sync(FULL, v, off2, LPR);
+                    Jrail = v;
+                } else {
+                    const int Jw = __reduce_add_sync(FULL, Jl);
+                    if (lane == 0 && Jw != 0) atomicAdd(&tr[0], Jw);
+                }
+            }
+            if constexpr (GRAD) {
+                // the current of step t pairs with the score of steps <= t
+                if (a.wJ && sl == 0 && seg < nact) {
+                    double *st = S.gS() + seg * 8;
+                    const long long tot = (long long)a.J_tot[t];
+                    const double b = a.loo > 0.0 ? __ddiv_rn((double)(tot - Jrail), a.loo) : 0.0;
+                    const double fJ = __dmul_rn(a.wJ[t], __dsub_rn((double)Jrail, b));
+                    st[2] = __dadd_rn(st[2], __dmul_rn(fJ, st[0]));
+                    st[3] = __dadd_rn(st[3], __dmul_rn(fJ, st[1]));
+                    st[4] = __dadd_rn(st[4], fJ);
+                }
             }
             __syncwarp();
         }
         // ---- flush this chunk's traces and counters
+        if constexpr (GRAD) continue;
         __syncthreads();
         const int nval = (c1 - c0) * (1 + Z);
         for (int i = threadIdx.x; i < nval; i += blockDim.x) {
@@ -860,6 +1074,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         __syncthreads();
     }
 
+    if constexpr (GRAD) {
+        if (active && sl == 0)
+            for (int i = 0; i < kGradState; ++i)
+                a.gstate[rail * kGradState + i] = S.gS()[seg * 8 + i];
+    }
+
     // ---- write the rail back
     if (active) {
         uint8_t *wrow = a.occ + rail * a.stride;
@@ -880,6 +1100,92 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
     extern __shared__ __align__(16) uint8_t smem[];
     const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);
     sweep_tile<LPR, WPL, ACC>(a, a.rk0, a.rk1, a.t0, a.n_steps, a.flush, tile_rail0, smem);
+}
+
+// Gradient pass: the forward sweep replayed from a checkpoint with the
+// likelihood-ratio score accumulated per rail (2 CTAs of 256 threads per SM).
+template <int LPR, int WPL>
+__global__ void __launch_bounds__(256, 2) sweep_grad_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);
+    sweep_tile<LPR, WPL, true, true>(a, a.rk0, a.rk1, a.t0, a.n_steps, a.flush, tile_rail0, smem);
+}
+
+// Per-rail gradient terms (d/dEa, d/dnu, d/dkappa, d/drho) from the state.
+__device__ __forceinline__ void rail_grad_terms(const double *gs, const int32_t *N0, int64_t r,
+                                                int L, double fill, int has_rho, double cEa,
+                                                double cnu, double v[4])
+{
+    const double *st = gs + r * kGradState;
+    v[0] = __dmul_rn(cEa, st[2]);
+    v[1] = __dmul_rn(cnu, st[2]);
+    v[2] = st[3];
+    v[3] = 0.0;
+    if (has_rho) {
+        // score of the rail's Bernoulli(fill) placement: (N0 - L fill) / (fill (1 - fill))
+        const double s0 = __ddiv_rn(__dsub_rn((double)N0[r], __dmul_rn((double)L, fill)),
+                                    __dmul_rn(fill, __dsub_rn(1.0, fill)));
+        v[3] = __dmul_rn(s0, st[4]);
+    }
+}
+
+// Deterministic sum of v over the 1024 threads of the block (result in thread 0).
+__device__ __forceinline__ void block_sum4(double v[4], double (*part)[4])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        for (int off = 16; off >= 1; off >>= 1) v[i] = __dadd_rn(v[i], __shfl_down_sync(FULL, v[i], off));
+    if (lane == 0)
+        for (int i = 0; i < 4; ++i) part[warp][i] = v[i];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int i = 0; i < 4; ++i) {
+            double x = lane < nw ? part[lane][i] : 0.0;
+            for (int off = 16; off >= 1; off >>= 1) x = __dadd_rn(x, __shfl_down_sync(FULL, x, off));
+            v[i] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum over rails of the per-rail terms (out[0..3]) and their standard error
+// sqrt(R / (R - 1) sum_r (G_r - mean)^2) (out[4..7]); one block, fixed order.
+__global__ void __launch_bounds__(1024) grad_reduce_kernel(const double *gs, int64_t R,
+                                                           const int32_t *N0, int L, double fill,
+                                                           int has_rho, double cEa, double cnu,
+                                                           double *out)
+{
+    __shared__ double part[32][4];
+    __shared__ double mean[4];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t r = threadIdx.x; r < R; r += blockDim.x) {
+        double v[4];
+        rail_grad_terms(gs, N0, r, L, fill, has_rho, cEa, cnu, v);
+        for (int i = 0; i < 4; ++i) acc[i] = __dadd_rn(acc[i], v[i]);
+    }
+    block_sum4(acc, part);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) {
+            out[i] = acc[i];
+            mean[i] = R > 0 ? __ddiv_rn(acc[i], (double)R) : 0.0;
+        }
+    __syncthreads();
+    double sq[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t r = threadIdx.x; r < R; r += blockDim.x) {
+        double v[4];
+        rail_grad_terms(gs, N0, r, L, fill, has_rho, cEa, cnu, v);
+        for (int i = 0; i < 4; ++i) {
+            const double dv = __dsub_rn(v[i], mean[i]);
+            sq[i] = __dadd_rn(sq[i], __dmul_rn(dv, dv));
+        }
+    }
+    block_sum4(sq, part);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i)
+            out[4 + i] = R > 1 ? sqrt(__dmul_rn(__ddiv_rn((double)R, (double)(R - 1)), sq[i])) : 0.0;
 }
 
 // Batch of devices in one persistent launch: CTAs take (device, rail tile)
@@ -934,12 +1240,22 @@ cudaError_t launch_t(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s)
 }
 
 template <int LPR, int WPL>
+cudaError_t grad_launch_t(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s)
+{
+    sweep_grad_kernel<LPR, WPL><<<l.grid, l.warps * 32, l.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LPR, int WPL>
 cudaError_t smem_attr()
 {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<LPR, WPL, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_kernel<LPR, WPL, true>,
+    e = cudaFuncSetAttribute(sweep_kernel<LPR, WPL, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_grad_kernel<LPR, WPL>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
@@ -956,6 +1272,39 @@ size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bo
     else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, persite, acc);
     else wb = Layout<32, 1>::bytes(Z, persite, acc);
     return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) + align16((size_t)L);
+}
+
+size_t grad_smem_bytes(int lpr, int wpl, int Z, int L, int warps)
+{
+    size_t wb = 0;
+    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, false, true) + Layout<32, 2>::grad_bytes(Z);
+    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, false, true) + Layout<1, 1>::grad_bytes(Z);
+    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, false, true) + Layout<2, 1>::grad_bytes(Z);
+    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, false, true) + Layout<4, 1>::grad_bytes(Z);
+    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, false, true) + Layout<8, 1>::grad_bytes(Z);
+    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, false, true) + Layout<16, 1>::grad_bytes(Z);
+    else wb = Layout<32, 1>::bytes(Z, false, true) + Layout<32, 1>::grad_bytes(Z);
+    return (size_t)warps * wb + align16((size_t)L);
+}
+
+cudaError_t grad_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s)
+{
+    if (l.wpl == 2) return grad_launch_t<32, 2>(a, l, s);
+    switch (l.lpr) {
+    case 1: return grad_launch_t<1, 1>(a, l, s);
+    case 2: return grad_launch_t<2, 1>(a, l, s);
+    case 4: return grad_launch_t<4, 1>(a, l, s);
+    case 8: return grad_launch_t<8, 1>(a, l, s);
+    case 16: return grad_launch_t<16, 1>(a, l, s);
+    default: return grad_launch_t<32, 1>(a, l, s);
+    }
+}
+
+cudaError_t grad_reduce(const double *gstate, int64_t R, const int32_t *N0, int L, double fill,
+                        int has_rho, double cEa, double cnu, double *out, cudaStream_t s)
+{
+    grad_reduce_kernel<<<1, 1024, 0, s>>>(gstate, R, N0, L, fill, has_rho, cEa, cnu, out);
+    return cudaGetLastError();
 }
 
 int sweep_pick_lpr(int L, int *wpl)

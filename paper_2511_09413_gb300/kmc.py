@@ -71,7 +71,7 @@ EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "
            "kmc_destroy", "kmc_last_error", "kmc_sweep_noalloc", "kmc_batch_create",
            "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
            "kmc_batch_current_step", "kmc_batch_destroy", "kmc_set_accept_path",
-           "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path"]
+           "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path", "kmc_grad"]
 
 _lib = None
 
@@ -115,13 +115,16 @@ def load(path: str = LIB_PATH):
     L.kmc_batch_current_step.restype = i64
     L.kmc_batch_destroy.argtypes = [vp]
     L.kmc_batch_destroy.restype = None
+    L.kmc_grad.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                           P(ctypes.c_double)]
     L.kmc_set_accept_path.argtypes = [vp, ctypes.c_int]
     L.kmc_accept_path.argtypes = [vp]
     L.kmc_batch_set_accept_path.argtypes = [vp, ctypes.c_int32]
     L.kmc_batch_accept_path.argtypes = [vp]
     for name in ("kmc_batch_create", "kmc_batch_step_n", "kmc_batch_observables",
                  "kmc_batch_set_launch", "kmc_batch_tune", "kmc_set_accept_path",
-                 "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path"):
+                 "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path",
+                 "kmc_grad"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables",
                  "kmc_set_voltage", "kmc_near_threshold_log", "kmc_counters", "kmc_set_launch"):
@@ -196,6 +199,24 @@ def kmc_counters(h: int) -> np.ndarray:
 
 def kmc_set_launch(h: int, warps_per_cta: int = 0, flush_steps: int = 0):
     _check(load().kmc_set_launch(ctypes.c_void_p(h), int(warps_per_cta), int(flush_steps)))
+
+
+def kmc_grad(h: int, n: int, Z: int, dLoss_dJ: Optional[np.ndarray] = None,
+             dLoss_dZc: Optional[np.ndarray] = None):
+    """(grad[4], stderr[4]) of E[F] with respect to (Ea, nu, kappa, fill) for
+    F = sum_s dLoss_dJ[s] J_s + sum_{s,z} dLoss_dZc[s, z] Zc_s[z] over the n
+    steps simulated so far."""
+    wJ = None if dLoss_dJ is None else np.ascontiguousarray(dLoss_dJ, dtype=np.float64)
+    wZ = None if dLoss_dZc is None else np.ascontiguousarray(dLoss_dZc, dtype=np.float64)
+    if wJ is not None and wJ.shape != (n,):
+        raise ValueError("dLoss_dJ must have shape (%d,)" % n)
+    if wZ is not None and wZ.shape != (n, Z):
+        raise ValueError("dLoss_dZc must have shape (%d, %d)" % (n, Z))
+    g = np.zeros(4)
+    se = np.zeros(4)
+    _check(load().kmc_grad(ctypes.c_void_p(h), _ptr(wJ, ctypes.c_double), _ptr(wZ, ctypes.c_double),
+                           _ptr(g, ctypes.c_double), _ptr(se, ctypes.c_double)))
+    return g, se
 
 
 def kmc_set_accept_path(h: int, mode: int = -1):
@@ -297,6 +318,11 @@ class Sim:
         occ = np.zeros((self.R, self.L), dtype=np.uint8)
         kmc_observables(self.h, 0, 0, None, None, occ)
         return occ
+
+    def grad(self, dLoss_dJ: Optional[np.ndarray] = None, dLoss_dZc: Optional[np.ndarray] = None):
+        """Likelihood-ratio gradient of E[F] (kmc_grad): (grad[4], stderr[4])
+        with respect to (Ea, nu, kappa, fill)."""
+        return kmc_grad(self.h, self.t, self.Z, dLoss_dJ, dLoss_dZc)
 
     def near_threshold_log(self, cap: int = 4096) -> np.ndarray:
         return kmc_near_threshold_log(self.h, cap)
