@@ -382,13 +382,137 @@ def run_batched(args):
     return 0
 
 
+def run_adjoint(args):
+    """Likelihood-ratio gradient of the mean relaxation current per replica
+    with respect to (Ea, nu, kappa, fill): 256 replicas of 4,096 x 512, 1 V x
+    1e4 steps then 5e4 relaxation steps.  Times the forward run and the
+    backward pass (kmc_grad).  With --fd-groups G > 0 it also compares, on
+    --fd-replicas replicas split into G independent groups, the LR gradient
+    with central differences (h = 1e-3 relative) under common random numbers,
+    and reports the GPU time each needs for equal standard error."""
+    import torch
+    from paper_2511_09413_gb300 import kmc
+
+    torch.cuda.set_device(0)
+    kmc.load()
+    stream = torch.cuda.current_stream()
+    n_write, n_relax = args.adj_write, args.adj_relax
+
+    def weights(replicas):
+        w = np.zeros(n_write + n_relax)
+        w[n_write:] = 1.0 / (n_relax * replicas)
+        return w
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    def run(replicas, instance, theta=None):
+        wl = W.adjoint_relaxation(replicas=replicas, n_write=n_write, n_relax=n_relax,
+                                  instance=instance)
+        d = wl.device
+        fill = wl.fill
+        if theta is not None:
+            d.Ea, d.nu, d.kappa, fill = theta
+        return wl, d, fill
+
+    # warm-up on a small device (loads the kernels, sets the allocator pools)
+    wl, d, fill = run(1, 0)
+    sim = kmc.Sim(d, wl.V, 1, fill=fill, stream=stream.cuda_stream)
+    sim.step_n(200)
+    sim.grad(weights(1)[:200], None)
+    sim.close()
+
+    wl, d, fill = run(args.replicas, 0)
+    sim = kmc.Sim(d, wl.V, 1, fill=fill, stream=stream.cuda_stream)
+    n = wl.n_steps
+    _, t_fwd = timed(lambda: sim.step_n(n))
+    (g, se), t_bwd = timed(lambda: sim.grad(weights(args.replicas), None))
+    J, _ = sim.traces()
+    sim.close()
+    su = d.R * d.L * n
+    names = ["Ea", "nu", "kappa", "fill"]
+    line = {
+        "metric": METRIC + ", adjoint", "value": su / (t_fwd + t_bwd), "unit": UNIT,
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * (t_fwd + t_bwd),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "replicas": args.replicas, "rails_per_replica": 4096,
+                   "sites": d.L, "fill": wl.fill, "dt_s": d.dt, "write": "1 V x %d steps" % n_write,
+                   "relaxation_steps": n_relax,
+                   "observable": "mean relaxation current per replica (ions/step)",
+                   "value_basis": "site-updates of the forward run / (forward + backward time)"},
+        "forward": {"site_updates_per_s": su / t_fwd, "s": t_fwd},
+        "backward": {"site_updates_per_s": su / t_bwd, "s": t_bwd},
+        "observable": float(J[n_write:].mean() / args.replicas),
+        "grad": dict(zip(names, g.tolist())), "grad_stderr": dict(zip(names, se.tolist())),
+    }
+    if args.fd_groups > 0:
+        G = args.fd_groups
+        per = max(1, args.fd_replicas // G)
+        lr, fd, t_lr, t_f = [], [], 0.0, 0.0
+        for grp in range(G):
+            wl, d, fill = run(per, 1000 + grp)
+            theta = [d.Ea, d.nu, d.kappa, fill]
+            sim = kmc.Sim(d, wl.V, 1, fill=fill, stream=stream.cuda_stream)
+            _, t1 = timed(lambda: sim.step_n(n))
+            (gg, _), t2 = timed(lambda: sim.grad(weights(per), None))
+            sim.close()
+            lr.append(gg)
+            t_lr += t1 + t2
+            row = []
+            for k in range(4):
+                h = 1e-3 * abs(theta[k])
+                vals = []
+                for sgn in (1.0, -1.0):
+                    th = list(theta)
+                    th[k] += sgn * h
+                    wl2, d2, fill2 = run(per, 1000 + grp, th)
+                    s2 = kmc.Sim(d2, wl2.V, 1, fill=fill2, stream=stream.cuda_stream)
+                    _, t3 = timed(lambda: s2.step_n(n))
+                    t_f += t3
+                    J2, _ = s2.traces()
+                    s2.close()
+                    vals.append(J2[n_write:].mean() / per)
+                row.append((vals[0] - vals[1]) / (2 * h))
+            fd.append(row)
+        lr, fd = np.array(lr), np.array(fd)
+        lm, ls = lr.mean(0), lr.std(0, ddof=1) / np.sqrt(G)
+        fm, fs = fd.mean(0), fd.std(0, ddof=1) / np.sqrt(G)
+        cost_lr = t_lr / G                  # one forward + one backward: all four entries
+        cost_fd = t_f / G / 4               # two forwards: one entry
+        line["fd_check"] = {
+            "replicas": per * G, "groups": G, "h_relative": 1e-3,
+            "lr": dict(zip(names, lm.tolist())), "lr_stderr": dict(zip(names, ls.tolist())),
+            "fd": dict(zip(names, fm.tolist())), "fd_stderr": dict(zip(names, fs.tolist())),
+            "z": dict(zip(names, ((lm - fm) / np.hypot(ls, fs)).tolist())),
+            "rel_diff": dict(zip(names, (np.abs(lm - fm) / np.abs(fm)).tolist())),
+            "gpu_s_per_group": {"lr_forward_backward": cost_lr, "fd_two_forwards": cost_fd},
+            # GPU time for one entry at equal standard error: FD / LR
+            "fd_over_lr_time_at_equal_error": dict(zip(names, (
+                (cost_fd * fs ** 2) / (cost_lr * ls ** 2)).tolist())),
+        }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kmc", "reference"], default="kmc")
-    ap.add_argument("--workload", choices=["hysteresis", "batched"], default="hysteresis")
+    ap.add_argument("--workload", choices=["hysteresis", "batched", "adjoint"], default="hysteresis")
+    ap.add_argument("--replicas", type=int, default=256, help="replicas in the adjoint workload")
+    ap.add_argument("--adj-write", type=int, default=10000, help="write-pulse steps (adjoint)")
+    ap.add_argument("--adj-relax", type=int, default=50000, help="relaxation steps (adjoint)")
+    ap.add_argument("--fd-groups", type=int, default=0, help="adjoint: groups of the FD check")
+    ap.add_argument("--fd-replicas", type=int, default=32, help="adjoint: replicas of the FD check")
     ap.add_argument("--instances", type=int, default=512, help="devices in the batched workload")
     ap.add_argument("--probe", type=int, default=1024, help="autotuner probe steps (batched)")
     ap.add_argument("--chunk", type=int, default=1000, help="time steps per benchmark step")
@@ -404,6 +528,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_kmc(args)
 
 

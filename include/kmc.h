@@ -156,7 +156,11 @@ int kmc_accept_path(const kmc_handle *h);
  * Bernoulli placement) and f_rs is the rail's share of F's step-s term minus
  * the mean share of the other rails (a baseline that leaves the estimate
  * unbiased).  Zone counts, recorded at the start of step s, pair with the
- * score of steps < s; the current of step s with that of steps <= s.
+ * score of steps < s; the current of step s with that of steps <= s, less
+ * dLoss_dJ[s] eta_rs times the score of steps < s, where eta_rs (the sum over
+ * the rail's left trials of a - p minus that over its right trials) is the
+ * part of the rail's current that the step's own draws add: a control
+ * variate of zero mean that removes most of the estimator's variance.
  * stderr_out (may be NULL) receives the standard error of each entry from the
  * spread of the independent per-rail terms.
  *

@@ -290,8 +290,10 @@ static int trial(double u, double p, orc_log_entry *log, int64_t cap, int64_t *c
 /*     d ln P0 / d Ea = -(x / kT) exp(-x) / P0,                              */
 /*     d ln P0 / d nu = (x / nu) exp(-x) / P0.                               */
 /* Electrode trials do not depend on Ea or nu.  The accumulator also sums   */
-/* the log-probability of the same outcomes under a second parameter set Pe */
-/* (for checking the derivatives by differences).                           */
+/* the innovation of the step's current, eta = sum over left trials of      */
+/* (a - p) minus the same over right trials (zero mean given the step-start */
+/* state), and the log-probability of the same outcomes under a second     */
+/* parameter set Pe (for checking the derivatives by differences).          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const orc_params *Pe;
@@ -301,6 +303,7 @@ typedef struct {
     double Be[ORC_MAX_ZONES], inve[ORC_MAX_ZONES];    /* B, 1/(1+B) at Pe */
     double s[3];                             /* score of the rail-step: Ea, nu, kappa */
     double ll;                               /* log-probability at Pe */
+    double eta;                              /* innovation of the step's current */
     int32_t Nz[ORC_MAX_ZONES];               /* zone counts of the step-start occupancy */
 } orc_trial_acc;
 
@@ -320,6 +323,7 @@ static void acc_begin(orc_trial_acc *a, const orc_params *P, const int32_t *Nz, 
     orc_zone_field(a->Pe, Nz, N0, V, dVe, a->Be, a->inve);
     a->s[0] = a->s[1] = a->s[2] = 0.0;
     a->ll = 0.0;
+    a->eta = 0.0;
 }
 
 static void acc_trial(orc_trial_acc *a, int z, int dir, int kind, double p, int hit)
@@ -331,6 +335,8 @@ static void acc_trial(orc_trial_acc *a, int z, int dir, int kind, double p, int 
         a->s[1] += w * a->dlnP0[1];
     }
     a->s[2] += w * dk;
+    /* a left trial that succeeds is a leftward crossing (+1 in J), a right one -1 */
+    a->eta += dir == 1 ? ((double)hit - p) : -((double)hit - p);
     const double base = kind == 0 ? a->P0e : (kind == 1 ? a->Ein_e : a->Eout_e);
     double pl, pr;
     orc_hop_probs(base, a->Be[z], a->inve[z], &pl, &pr);
@@ -574,6 +580,13 @@ int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64
                         fZ += wZ[s * Z + z] * ((double)acc.Nz[z] - b);
                     }
                     for (int i = 0; i < 4; ++i) Gr[i] += fZ * Sr[i];
+                }
+                /* control variate: the innovation of J_rs times the score before step s
+                 * has zero mean; removing it leaves the predictable part of the
+                 * current paired with the past score */
+                if (wJ) {
+                    const double c = wJ[s] * acc.eta;
+                    for (int i = 0; i < 4; ++i) Gr[i] -= c * Sr[i];
                 }
                 for (int i = 0; i < 3; ++i) Sr[i] += acc.s[i];
                 /* the current of step t pairs with the score of steps <= t */

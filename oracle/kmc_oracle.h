@@ -67,12 +67,14 @@ int orc_max_threads(void);
  * score S_cum[r] = (d/dEa, d/dnu, d/dkappa, d/drho) log-probability of the
  * rail's trajectory so far (entry 3, the initial-placement score, is set by
  * the caller and left unchanged), and adds to G[r]
- *     fZ_s S_cum(before step s) + fJ_s S_cum(after step s),
+ *     (fZ_s - wJ[s] eta_rs) S_cum(before step s) + fJ_s S_cum(after step s),
  *     fJ_s = wJ[s] (J_rs - (J_tot[s] - J_rs) / (R - 1)),
+ *     eta_rs = sum over the rail's left trials of (a - p) - same over right trials,
  *     fZ_s = sum_z wZ[s][z] (N_rz(s) - (Zc_tot[s][z] - N_rz(s)) / (R - 1)),
  * with the totals J_tot, Zc_tot of the same run (leave-one-out baselines;
  * none when R == 1).  The sum of G over rails estimates dE[F]/dtheta without
- * bias.  loglik[r] (optional) accumulates the log-probability of the same
+ * bias (the eta term is a control variate: eta_rs has zero mean given the
+ * state at the start of step s, and S_cum before step s is fixed by then).  loglik[r] (optional) accumulates the log-probability of the same
  * trial outcomes under parameters Pe.  J_out (optional) receives J_s. */
 int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64_t t0,
                int64_t n_steps, uint8_t *occ, const int32_t *N0, const double *wJ,

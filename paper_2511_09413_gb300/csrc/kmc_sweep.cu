@@ -137,12 +137,17 @@ struct Layout {
         return FIXED + rm_bytes(Z, acc) + 2 * gz8(Z) + pb_bytes(Z) +
                (persite ? align16((size_t)4 * 1024 * WPL) : 0);
     }
-    // gradient pass, appended: accepted-trial masks accR, accL uint32 [W] each,
-    // Q_z double [G][Z] (gzq = align16(8 G Z) bytes), (W_z, K_z) double2 [G][Z]
-    // (2 gzq bytes), per-rail state double [G][8]
+    // gradient pass, appended: accepted-trial masks accR, accL uint32 [W] each;
+    // per (rail, zone) (gzq = align16(8 G Z) bytes per double): Q_z double,
+    // (W_z, K_z) double2, and the cached (p_R, p_L), (1/(1-p_R), 1/(1-p_L)),
+    // (d ln p_R / d kappa, d ln p_L / d kappa) double2, the current's innovation
+    // eta_z double; per rail double [G][16]
+    // (state, Qbar, V of the cache, electrode probabilities and reciprocals);
+    // per rail int [G][Z+2] (zone prefix counts of the cache, changed flag)
     __host__ __device__ static size_t grad_bytes(int Z)
     {
-        return 2 * align16(4 * W) + 3 * align16((size_t)8 * G * Z) + align16((size_t)64 * G);
+        return 2 * align16(4 * W) + 10 * align16((size_t)8 * G * Z) + align16((size_t)128 * G) +
+               align16((size_t)4 * G * (Z + 2));
     }
 };
 
@@ -177,15 +182,15 @@ struct WarpSmem {
     __device__ float *P0f() const { return (float *)(b + Ly::FIXED + rz + 2 * gz + pbz); }
     __device__ uint32_t *accR() const { return (uint32_t *)(b + goff); }
     __device__ uint32_t *accL() const { return (uint32_t *)(b + goff + align16(4 * Ly::W)); }
-    __device__ double *gQ() const { return (double *)(b + goff + 2 * align16(4 * Ly::W)); }
-    __device__ double2 *gWK() const
-    {
-        return (double2 *)(b + goff + 2 * align16(4 * Ly::W) + gzq);
-    }
-    __device__ double *gS() const
-    {
-        return (double *)(b + goff + 2 * align16(4 * Ly::W) + 3 * gzq);
-    }
+    __device__ uint8_t *gbase() const { return b + goff + 2 * align16(4 * Ly::W); }
+    __device__ double *gQ() const { return (double *)gbase(); }
+    __device__ double2 *gWK() const { return (double2 *)(gbase() + gzq); }
+    __device__ double2 *gP() const { return (double2 *)(gbase() + 3 * gzq); }
+    __device__ double2 *gR1() const { return (double2 *)(gbase() + 5 * gzq); }
+    __device__ double2 *gDK() const { return (double2 *)(gbase() + 7 * gzq); }
+    __device__ double *gEta() const { return (double *)(gbase() + 9 * gzq); }
+    __device__ double *gS() const { return (double *)(gbase() + 10 * gzq); }
+    __device__ int32_t *gPb() const { return (int32_t *)(gbase() + 10 * gzq + align16(128 * Ly::G)); }
 };
 
 // --------------------------------------------------------- exact FP64 path
@@ -388,12 +393,12 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
 // ------------------------------------------------- likelihood-ratio score
 // Summed score weight of n Bernoulli(p) trials of which A succeeded: each
 // trial contributes (a - p) / (1 - p) times d ln p (a certain trial, p >= 1,
-// contributes d ln p).
-__device__ __forceinline__ double trial_weight(int A, int n, double p)
+// contributes d ln p); r1p is 1 / (1 - p), kept with p.
+__device__ __forceinline__ double trial_weight(int A, int n, double p, double r1p)
 {
     if (n == 0) return 0.0;
     if (p >= 1.0) return (double)A;
-    return __ddiv_rn(__dsub_rn((double)A, __dmul_rn((double)n, p)), __dsub_rn(1.0, p));
+    return __dmul_rn(__dsub_rn((double)A, __dmul_rn((double)n, p)), r1p);   // r1p = 1 / (1 - p)
 }
 
 // Score of one step for the rails of a warp (gradient pass).  Trials are
@@ -412,41 +417,74 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
     const int L = a.L, Z = a.Z;
     const DevConst &K = *a.K;
     const double V = a.V[t];
-    // enclosed charge Q_z and its rail mean, one lane per rail, oracle order
+    // A. per rail: is the cache of (rail, zone) probabilities stale (V or any
+    //    zone count changed)?  If so, the enclosed charge Q_z and its rail mean,
+    //    in the oracle's operation order.
     if (lane % LPR == 0 && lane / LPR < nact) {
         const int g = lane / LPR;
         const int32_t *Pb = S.Pb() + g * (Z + 1);
-        const double Ld = (double)L;
-        const int32_t n0 = S.N0s()[g];
-        double run = 0.0, acc = 0.0;
-        for (int z = 0; z < Z; ++z) {
-            const int w = K.bnd[z + 1] - K.bnd[z];
-            const int Nz = Pb[z + 1] - Pb[z];
-            const double C = __dsub_rn((double)Nz, __ddiv_rn(__dmul_rn((double)n0, (double)w), Ld));
-            const double Q = __dadd_rn(run, __dmul_rn(0.5, C));
-            run = __dadd_rn(run, C);
-            acc = __dadd_rn(acc, __dmul_rn((double)w, Q));
-            S.gQ()[g * Z + z] = Q;
+        int32_t *Pc = S.gPb() + g * (Z + 2);
+        double *rs = S.gS() + g * 16;
+        bool changed = !(rs[6] == V);
+        for (int z = 0; z <= Z; ++z) changed |= Pb[z] != Pc[z];
+        Pc[Z + 1] = changed ? 1 : 0;
+        if (changed) {
+            for (int z = 0; z <= Z; ++z) Pc[z] = Pb[z];
+            rs[6] = V;
+            const double Ld = (double)L;
+            const int32_t n0 = S.N0s()[g];
+            double run = 0.0, acc = 0.0;
+            for (int z = 0; z < Z; ++z) {
+                const int w = K.bnd[z + 1] - K.bnd[z];
+                const int Nz = Pb[z + 1] - Pb[z];
+                const double C = __dsub_rn((double)Nz, __ddiv_rn(__dmul_rn((double)n0, (double)w), Ld));
+                const double Q = __dadd_rn(run, __dmul_rn(0.5, C));
+                run = __dadd_rn(run, C);
+                acc = __dadd_rn(acc, __dmul_rn((double)w, Q));
+                S.gQ()[g * Z + z] = Q;
+            }
+            rs[5] = __ddiv_rn(acc, Ld);
         }
-        S.gS()[g * 8 + 5] = __ddiv_rn(acc, Ld);
     }
     __syncwarp();
     for (int pi = lane; pi < G * Z; pi += 32) {
         const int g = pi / Z, z = pi - g * Z;
         if (g >= nact) continue;
-        // Eqs. 3-6 in the oracle's operation order
-        const double dq = __dsub_rn(S.gQ()[pi], S.gS()[g * 8 + 5]);
-        const double dV = __dsub_rn(V, __dmul_rn(K.ka, dq));
-        const double dE = __ddiv_rn(__dmul_rn(dV, K.d), K.t_dev);
-        const double B = exp(__ddiv_rn(-dE, K.kT));
-        const double inv = __ddiv_rn(1.0, __dadd_rn(1.0, B));
-        const double pL = __dmul_rn(K.P0, inv);
-        const double pR = __dmul_rn(pL, B);
-        const double c = __ddiv_rn(__dmul_rn(__dmul_rn(a.alpha, dq), K.d), a.tdev_kT);
-        const double dkR = __dmul_rn(inv, c);
-        const double dkL = -__dmul_rn(__dsub_rn(1.0, inv), c);
-        // inner trials of the zone's sites [lo, hi); at an open rail the outward
-        // trials of sites 0 and L-1 are electrode trials, counted below
+        double *rs = S.gS() + g * 16;
+        if (S.gPb()[g * (Z + 2) + Z + 1]) {
+            // B1. Eqs. 3-6 in the oracle's operation order, cached until the
+            //     rail's zone counts or V change
+            const double dq = __dsub_rn(S.gQ()[pi], rs[5]);
+            const double dV = __dsub_rn(V, __dmul_rn(K.ka, dq));
+            const double dE = __ddiv_rn(__dmul_rn(dV, K.d), K.t_dev);
+            const double B = exp(__ddiv_rn(-dE, K.kT));
+            const double inv = __ddiv_rn(1.0, __dadd_rn(1.0, B));
+            const double pL = __dmul_rn(K.P0, inv);
+            const double pR = __dmul_rn(pL, B);
+            const double c = __ddiv_rn(__dmul_rn(__dmul_rn(a.alpha, dq), K.d), a.tdev_kT);
+            S.gP()[pi] = make_double2(pR, pL);
+            S.gR1()[pi] = make_double2(pR < 1.0 ? __drcp_rn(__dsub_rn(1.0, pR)) : 0.0,
+                                       pL < 1.0 ? __drcp_rn(__dsub_rn(1.0, pL)) : 0.0);
+            S.gDK()[pi] = make_double2(__dmul_rn(inv, c), -__dmul_rn(__dsub_rn(1.0, inv), c));
+            if (open && z == 0) {
+                const double pin = __dmul_rn(__dmul_rn(K.E_in, inv), B);   // injection into 0
+                const double pout = __dmul_rn(K.E_out, inv);               // extraction at 0
+                rs[7] = pin;
+                rs[8] = pout;
+                rs[11] = pin < 1.0 ? __drcp_rn(__dsub_rn(1.0, pin)) : 0.0;
+                rs[12] = pout < 1.0 ? __drcp_rn(__dsub_rn(1.0, pout)) : 0.0;
+            }
+            if (open && z == Z - 1) {
+                const double pout = __dmul_rn(__dmul_rn(K.E_out, inv), B);  // extraction at L-1
+                const double pin = __dmul_rn(K.E_in, inv);                  // injection into L-1
+                rs[9] = pout;
+                rs[10] = pin;
+                rs[13] = pout < 1.0 ? __drcp_rn(__dsub_rn(1.0, pout)) : 0.0;
+                rs[14] = pin < 1.0 ? __drcp_rn(__dsub_rn(1.0, pin)) : 0.0;
+            }
+        }
+        // B2. inner trials of the zone's sites [lo, hi); at an open rail the
+        //     outward trials of sites 0 and L-1 are electrode trials, below
         const int lo = K.bnd[z], hi = K.bnd[z + 1];
         int nR = 0, nL = 0, aR = 0, aL = 0;
         for (int w = lo >> 5; w <= (hi - 1) >> 5; ++w) {
@@ -466,31 +504,40 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
             aR += __popc(o & fR & S.accR()[idx]);
             aL += __popc(o & fL & S.accL()[idx]);
         }
-        const double wR = trial_weight(aR, nR, pR), wL = trial_weight(aL, nL, pL);
+        const double2 p = S.gP()[pi], r1 = S.gR1()[pi], dk = S.gDK()[pi];
+        const double wR = trial_weight(aR, nR, p.x, r1.x), wL = trial_weight(aL, nL, p.y, r1.y);
         const double Wz = __dadd_rn(wR, wL);
-        double Kz = __dadd_rn(__dmul_rn(wR, dkR), __dmul_rn(wL, dkL));
+        double Kz = __dadd_rn(__dmul_rn(wR, dk.x), __dmul_rn(wL, dk.y));
+        // innovation of the current: left trials (a - p) minus right trials (a - p)
+        double Ez = __dsub_rn(__dsub_rn((double)aL, __dmul_rn((double)nL, p.y)),
+                              __dsub_rn((double)aR, __dmul_rn((double)nR, p.x)));
         if (open && z == 0) {
             const int idx = g * LPR * WPL;
             if (S.ow()[idx] & 1u) {        // extraction through the left electrode
-                const double pe = __dmul_rn(K.E_out, inv);
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accL()[idx] & 1u) ? 1 : 0, 1, pe), dkL));
+                const int hit = (S.accL()[idx] & 1u) ? 1 : 0;
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[8], rs[12]), dk.y));
+                Ez = __dadd_rn(Ez, __dsub_rn((double)hit, rs[8]));
             } else {                       // injection into site 0
-                const double pe = __dmul_rn(__dmul_rn(K.E_in, inv), B);
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accR()[idx] & 1u) ? 1 : 0, 1, pe), dkR));
+                const int hit = (S.accR()[idx] & 1u) ? 1 : 0;
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[7], rs[11]), dk.x));
+                Ez = __dsub_rn(Ez, __dsub_rn((double)hit, rs[7]));
             }
         }
         if (open && z == Z - 1) {
             const int idx = g * LPR * WPL + ((L - 1) >> 5);
             const uint32_t bit = 1u << ((L - 1) & 31);
             if (S.ow()[idx] & bit) {       // extraction through the right electrode
-                const double pe = __dmul_rn(__dmul_rn(K.E_out, inv), B);
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accR()[idx] & bit) ? 1 : 0, 1, pe), dkR));
+                const int hit = (S.accR()[idx] & bit) ? 1 : 0;
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[9], rs[13]), dk.x));
+                Ez = __dsub_rn(Ez, __dsub_rn((double)hit, rs[9]));
             } else {                       // injection into site L-1
-                const double pe = __dmul_rn(K.E_in, inv);
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight((S.accL()[idx] & bit) ? 1 : 0, 1, pe), dkL));
+                const int hit = (S.accL()[idx] & bit) ? 1 : 0;
+                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[10], rs[14]), dk.y));
+                Ez = __dadd_rn(Ez, __dsub_rn((double)hit, rs[10]));
             }
         }
         S.gWK()[pi] = make_double2(Wz, Kz);
+        S.gEta()[pi] = Ez;
     }
     __syncwarp();
 }
@@ -557,9 +604,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         }
     }
     if constexpr (GRAD) {
+        if (sl == 0) S.gS()[seg * 16 + 6] = __longlong_as_double(0x7FF8000000000000ll);  // no cache
         if (sl == 0)
             for (int i = 0; i < kGradState; ++i)
-                S.gS()[seg * 8 + i] = active ? a.gstate[rail * kGradState + i] : 0.0;
+                S.gS()[seg * 16 + i] = active ? a.gstate[rail * kGradState + i] : 0.0;
     }
     for (int i = lane; i < 2 * G; i += 32) S.inj()[i] = 0;
     if (sl == 0) S.N0s()[seg] = active ? a.N0[rail] : 0;
@@ -935,12 +983,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 __syncwarp();
                 grad_step_score<LPR, WPL>(a, S, t, nact, open, lane);
                 if (sl == 0 && seg < nact) {
-                    double *st = S.gS() + seg * 8;       // W, K, G_W, G_K, G_1
-                    double Ws = 0.0, Ks = 0.0;
+                    double *st = S.gS() + seg * 16;      // W, K, G_W, G_K, G_1
+                    double Ws = 0.0, Ks = 0.0, Es = 0.0;
                     for (int z = 0; z < Z; ++z) {
                         const double2 wk = S.gWK()[seg * Z + z];
                         Ws = __dadd_rn(Ws, wk.x);
                         Ks = __dadd_rn(Ks, wk.y);
+                        Es = __dadd_rn(Es, S.gEta()[seg * Z + z]);
                     }
                     if (a.wZ) {
                         // zone counts at the start of step t pair with the score of steps < t
@@ -954,6 +1003,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         st[2] = __dadd_rn(st[2], __dmul_rn(fZ, st[0]));
                         st[3] = __dadd_rn(st[3], __dmul_rn(fZ, st[1]));
                         st[4] = __dadd_rn(st[4], fZ);
+                    }
+                    if (a.wJ) {
+                        // control variate: the current's innovation times the score
+                        // before this step has zero mean
+                        const double c = __dmul_rn(a.wJ[t], Es);
+                        st[2] = __dsub_rn(st[2], __dmul_rn(c, st[0]));
+                        st[3] = __dsub_rn(st[3], __dmul_rn(c, st[1]));
+                        st[4] = __dsub_rn(st[4], c);
                     }
                     st[0] = __dadd_rn(st[0], Ws);
                     st[1] = __dadd_rn(st[1], Ks);
@@ -1039,7 +1096,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             if constexpr (GRAD) {
                 // the current of step t pairs with the score of steps <= t
                 if (a.wJ && sl == 0 && seg < nact) {
-                    double *st = S.gS() + seg * 8;
+                    double *st = S.gS() + seg * 16;
                     const long long tot = (long long)a.J_tot[t];
                     const double b = a.loo > 0.0 ? __ddiv_rn((double)(tot - Jrail), a.loo) : 0.0;
                     const double fJ = __dmul_rn(a.wJ[t], __dsub_rn((double)Jrail, b));
@@ -1077,7 +1134,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     if constexpr (GRAD) {
         if (active && sl == 0)
             for (int i = 0; i < kGradState; ++i)
-                a.gstate[rail * kGradState + i] = S.gS()[seg * 8 + i];
+                a.gstate[rail * kGradState + i] = S.gS()[seg * 16 + i];
     }
 
     // ---- write the rail back

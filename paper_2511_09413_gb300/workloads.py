@@ -173,3 +173,19 @@ def stdp_batch(n_inst: int = 512, seed: int = 7, n_steps: Optional[int] = None,
         fills.append(fill)
         delays.append(d)
     return devs, Vs, fills, delays
+
+
+def adjoint_relaxation(replicas: int = 256, rails: int = 4096, L: int = 512, fill: float = 0.2,
+                       n_write: int = 10000, n_relax: int = 50000, V_write: float = 1.0,
+                       seed: int = 13, instance: int = 0) -> Workload:
+    """Write pulse and relaxation on independent replicas of a 4,096-rail x
+    512-site device, 20 % Bernoulli filling, Ea = 0.40 eV, dt = 5e-7 s
+    (2,000 steps per ms), blocking electrodes: V_write for n_write steps, then
+    0 V for n_relax steps.  Rails are independent, so the replicas are laid end
+    to end as one device of replicas x rails rails (rail index r of replica q
+    is q * rails + r; every rail has its own Philox counters)."""
+    dev = Device(R=replicas * rails, L=L, Z=10, electrodes=0, dt=5e-7, seed=seed,
+                 instance=instance)
+    return Workload("adjoint_relaxation_%dx%dx%d" % (replicas, rails, L), dev,
+                    relaxation_protocol(n_write, V_write, n_write + n_relax, 0.0),
+                    init_mode=1, fill=fill)
