@@ -495,12 +495,14 @@ int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, dou
             h->g_occ = (uint8_t *)h->alloc(occ_bytes);
             h->g_state = (double *)h->alloc(sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1));
             h->g_wJ = (double *)h->alloc(sizeof(double) * nt);
-            h->g_wZ = (double *)h->alloc(sizeof(double) * nt * (size_t)Z);
+            h->g_fJab = (double *)h->alloc(sizeof(double) * 2 * nt);
+            h->g_fZa = (double *)h->alloc(sizeof(double) * nt * (size_t)Z);
+            h->g_fZb = (double *)h->alloc(sizeof(double) * nt);
             h->g_out = (double *)h->alloc(sizeof(double) * 8);
             h->g_misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
             h->g_args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
-            if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_wZ || !h->g_out || !h->g_misc ||
-                !h->g_args_dev)
+            if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_fJab || !h->g_fZa || !h->g_fZb ||
+                !h->g_out || !h->g_misc || !h->g_args_dev)
                 return fail(KMC_E_NOMEM, "device allocation failed (gradient pass)");
         }
         for (int64_t i = 0; i < n; ++i)
@@ -510,13 +512,49 @@ int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, dou
             for (int64_t i = 0; i < n * Z; ++i)
                 if (!isfinite(dLoss_dZc[i]))
                     return fail(KMC_E_ARG, "dLoss_dZc[%lld] is not finite", (long long)i);
-        if (dLoss_dJ)
+        // the forward's totals give each step's leave-one-out baseline:
+        //   fJ = wJ (J_r - (J_t - J_r) / (R - 1)) = aJ J_r - bJ, and likewise fZ
+        std::vector<int64_t> Jt((size_t)n), Zt;
+        CK(cudaMemcpyAsync(Jt.data(), h->J, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s),
+           "copy J");
+        if (dLoss_dZc) {
+            Zt.resize((size_t)(n * Z));
+            CK(cudaMemcpyAsync(Zt.data(), h->Zc, sizeof(int64_t) * (size_t)(n * Z),
+                               cudaMemcpyDeviceToHost, s),
+               "copy Zc");
+        }
+        CK(cudaStreamSynchronize(s), "totals");
+        const double loo = R > 1 ? (double)(R - 1) : 0.0;
+        const double scale = R > 1 ? (double)R / loo : 1.0;
+        std::vector<double> fJab, fZa, fZb;
+        if (dLoss_dJ) {
+            fJab.resize((size_t)(2 * n));
+            for (int64_t i = 0; i < n; ++i) {
+                fJab[2 * i] = dLoss_dJ[i] * scale;
+                fJab[2 * i + 1] = loo > 0.0 ? dLoss_dJ[i] * ((double)Jt[i] / loo) : 0.0;
+            }
             CK(cudaMemcpyAsync(h->g_wJ, dLoss_dJ, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s),
                "copy dLoss_dJ");
-        if (dLoss_dZc)
-            CK(cudaMemcpyAsync(h->g_wZ, dLoss_dZc, sizeof(double) * (size_t)(n * Z),
+            CK(cudaMemcpyAsync(h->g_fJab, fJab.data(), sizeof(double) * (size_t)(2 * n),
                                cudaMemcpyHostToDevice, s),
-               "copy dLoss_dZc");
+               "copy fJ coefficients");
+        }
+        if (dLoss_dZc) {
+            fZa.resize((size_t)(n * Z));
+            fZb.assign((size_t)n, 0.0);
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t z = 0; z < Z; ++z) {
+                    const double w = dLoss_dZc[i * Z + z];
+                    fZa[(size_t)(i * Z + z)] = w * scale;
+                    if (loo > 0.0) fZb[(size_t)i] += w * ((double)Zt[(size_t)(i * Z + z)] / loo);
+                }
+            CK(cudaMemcpyAsync(h->g_fZa, fZa.data(), sizeof(double) * (size_t)(n * Z),
+                               cudaMemcpyHostToDevice, s),
+               "copy fZ coefficients");
+            CK(cudaMemcpyAsync(h->g_fZb, fZb.data(), sizeof(double) * (size_t)n,
+                               cudaMemcpyHostToDevice, s),
+               "copy fZ offsets");
+        }
         CK(cudaMemcpyAsync(h->g_occ, h->occ_init, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
         CK(cudaMemsetAsync(h->g_state, 0, sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1), s),
            "memset");
@@ -532,11 +570,10 @@ int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, dou
         ga.log_count = h->g_misc;
         ga.counters = h->g_misc + 1;
         ga.wJ = dLoss_dJ ? h->g_wJ : nullptr;
-        ga.wZ = dLoss_dZc ? h->g_wZ : nullptr;
-        ga.J_tot = h->J;
-        ga.Zc_tot = h->Zc;
+        ga.fJab = dLoss_dJ ? (const double2 *)h->g_fJab : nullptr;
+        ga.fZa = dLoss_dZc ? h->g_fZa : nullptr;
+        ga.fZb = dLoss_dZc ? h->g_fZb : nullptr;
         ga.gstate = h->g_state;
-        ga.loo = R > 1 ? (double)(R - 1) : 0.0;
         ga.alpha = p.alpha_V;
         const double kT = 8.6173e-5 * p.T_K;
         ga.tdev_kT = ((double)L * p.site_spacing_nm) * kT;

@@ -48,7 +48,9 @@ struct kmc_handle {
     // gradient pass (allocated at the first kmc_grad)
     uint8_t *g_occ = nullptr;                 // replayed occupancy
     double *g_state = nullptr;                // [R][kGradState]
-    double *g_wJ = nullptr, *g_wZ = nullptr;  // observable weights per step
+    double *g_wJ = nullptr;                   // weight of J_t per step
+    double *g_fJab = nullptr;                 // per step (aJ, bJ): baselined current share
+    double *g_fZa = nullptr, *g_fZb = nullptr;  // per step aZ[Z], bZ: baselined zone share
     double *g_out = nullptr;                  // [8] sums and standard errors
     unsigned long long *g_misc = nullptr;     // log count and counters of the replay
     kmc::SweepArgs *g_args_dev = nullptr;

@@ -64,12 +64,16 @@ struct SweepArgs {
     float E_inf, E_outf;          // electrode base probabilities in FP32
 
     // likelihood-ratio gradient pass only (unused by the forward sweep)
-    const double *wJ;                    // [n_steps_total] weight of J_t in the observable
-    const double *wZ;                    // [n_steps_total][Z] weight of Zc_t[z], or null
-    const unsigned long long *J_tot;     // [n_steps_total] the forward's J_t
-    const unsigned long long *Zc_tot;    // [n_steps_total][Z] the forward's Zc_t
+    // With the forward's totals J_t, Zc_t and the leave-one-out divisor R - 1,
+    // a rail's baselined share of the observable's step-t terms is
+    //   fJ = aJ J_rt - bJ,  aJ = wJ_t R / (R - 1),  bJ = wJ_t J_t / (R - 1),
+    //   fZ = sum_z aZ_z N_rz - bZ,  aZ_z = wZ_tz R / (R - 1),  bZ = sum_z wZ_tz Zc_tz / (R - 1)
+    // (aJ = wJ_t, bJ = 0 and the like when R == 1), precomputed on the host.
+    const double *wJ;                    // [n_steps_total] weight of J_t, or null
+    const double2 *fJab;                 // [n_steps_total] (aJ, bJ)
+    const double *fZa;                   // [n_steps_total][Z] aZ, or null
+    const double *fZb;                   // [n_steps_total] bZ
     double *gstate;                      // [R][kGradState] per-rail accumulators
-    double loo;                          // R - 1 (leave-one-out divisor), 0 when R == 1
     double alpha;                        // space-charge volts per excess ion
     double tdev_kT;                      // t_dev kB T (d ln B / d kappa denominator)
 };

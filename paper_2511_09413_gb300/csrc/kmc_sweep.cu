@@ -139,9 +139,9 @@ struct Layout {
     }
     // gradient pass, appended: accepted-trial masks accR, accL uint32 [W] each;
     // per (rail, zone) (gzq = align16(8 G Z) bytes per double): Q_z double,
-    // (W_z, K_z) double2, and the cached (p_R, p_L), (1/(1-p_R), 1/(1-p_L)),
-    // (d ln p_R / d kappa, d ln p_L / d kappa) double2, the current's innovation
-    // eta_z double; per rail double [G][16]
+    // N0 w_z / L double, and the cached (p_R, p_L), (1/(1-p_R), 1/(1-p_L)),
+    // (d ln p_R / d kappa, d ln p_L / d kappa), (p_R/(1-p_R), p_L/(1-p_L))
+    // double2; per rail double [G][16]
     // (state, Qbar, V of the cache, electrode probabilities and reciprocals);
     // per rail int [G][Z+2] (zone prefix counts of the cache, changed flag)
     __host__ __device__ static size_t grad_bytes(int Z)
@@ -184,11 +184,11 @@ struct WarpSmem {
     __device__ uint32_t *accL() const { return (uint32_t *)(b + goff + align16(4 * Ly::W)); }
     __device__ uint8_t *gbase() const { return b + goff + 2 * align16(4 * Ly::W); }
     __device__ double *gQ() const { return (double *)gbase(); }
-    __device__ double2 *gWK() const { return (double2 *)(gbase() + gzq); }
-    __device__ double2 *gP() const { return (double2 *)(gbase() + 3 * gzq); }
-    __device__ double2 *gR1() const { return (double2 *)(gbase() + 5 * gzq); }
-    __device__ double2 *gDK() const { return (double2 *)(gbase() + 7 * gzq); }
-    __device__ double *gEta() const { return (double *)(gbase() + 9 * gzq); }
+    __device__ double *gCz() const { return (double *)(gbase() + gzq); }
+    __device__ double2 *gP() const { return (double2 *)(gbase() + 2 * gzq); }
+    __device__ double2 *gR1() const { return (double2 *)(gbase() + 4 * gzq); }
+    __device__ double2 *gDK() const { return (double2 *)(gbase() + 6 * gzq); }
+    __device__ double2 *gPQ() const { return (double2 *)(gbase() + 8 * gzq); }
     __device__ double *gS() const { return (double *)(gbase() + 10 * gzq); }
     __device__ int32_t *gPb() const { return (int32_t *)(gbase() + 10 * gzq + align16(128 * Ly::G)); }
 };
@@ -392,154 +392,176 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
 
 // ------------------------------------------------- likelihood-ratio score
 // Summed score weight of n Bernoulli(p) trials of which A succeeded: each
-// trial contributes (a - p) / (1 - p) times d ln p (a certain trial, p >= 1,
-// contributes d ln p); r1p is 1 / (1 - p), kept with p.
-__device__ __forceinline__ double trial_weight(int A, int n, double p, double r1p)
+// trial contributes (a - p) / (1 - p) times d ln p, so the sum is
+// A / (1 - p) - n p / (1 - p) (a certain trial, p >= 1, contributes d ln p).
+// r1 = 1 / (1 - p) and q = p / (1 - p) are kept with p.
+__device__ __forceinline__ double trial_weight(int A, int n, double p, double r1, double q)
 {
     if (n == 0) return 0.0;
     if (p >= 1.0) return (double)A;
-    return __dmul_rn(__dsub_rn((double)A, __dmul_rn((double)n, p)), r1p);   // r1p = 1 / (1 - p)
+    return __fma_rn(-(double)n, q, __dmul_rn((double)A, r1));
 }
 
 // Score of one step for the rails of a warp (gradient pass).  Trials are
 // grouped per (rail, zone): inner hops of a zone share p (scalar barrier), so
 // their summed weight needs only the counts of performed and accepted trials
 // from the step-start masks ow, fR, fL and the accepted-trial masks; the
-// electrode trials of the two boundary sites are added one by one.  Writes
-// (W_z, K_z) per (rail, zone): the summed inner-trial weight (times
-// d ln P0 / d theta it is the Ea and nu score) and the kappa score with
-// d ln p / d kappa = (s - B/(1+B)) d ln B / d kappa, s = 1 right, 0 left.
+// electrode trials of the two boundary sites are added one by one.  Lane sl
+// of rail slot seg takes zones sl, sl + W2, ... (W2, a power of two <= LPR,
+// lanes per rail take part) and the partial sums are reduced over them.  In
+// lane sl == 0 it returns Ws, the summed inner-trial weight (times
+// d ln P0 / d theta it is the Ea and nu score), Ks, the kappa score with
+// d ln p / d kappa = (s - B/(1+B)) d ln B / d kappa (s = 1 right, 0 left),
+// and Es, the innovation of the rail's current (left trials' a - p minus
+// right trials' a - p).  The per-zone probabilities (Eqs. 3-6, FP64, the
+// oracle's operation order) are cached until the rail's zone counts or V
+// change.
 template <int LPR, int WPL>
 __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSmem<LPR, WPL> &S,
-                                                uint32_t t, int nact, bool open, int lane)
+                                                uint32_t t, int nact, bool open, int seg, int sl,
+                                                int W2, double gInvL, double gXV, double gKC,
+                                                double &Ws, double &Ks, double &Es)
 {
-    constexpr int G = 32 / LPR;
     const int L = a.L, Z = a.Z;
     const DevConst &K = *a.K;
     const double V = a.V[t];
-    // A. per rail: is the cache of (rail, zone) probabilities stale (V or any
-    //    zone count changed)?  If so, the enclosed charge Q_z and its rail mean,
-    //    in the oracle's operation order.
-    if (lane % LPR == 0 && lane / LPR < nact) {
-        const int g = lane / LPR;
-        const int32_t *Pb = S.Pb() + g * (Z + 1);
-        int32_t *Pc = S.gPb() + g * (Z + 2);
-        double *rs = S.gS() + g * 16;
+    const bool act = seg < nact;
+    // A. one lane per rail: is the cache stale (V or a zone count changed)?
+    if (sl == 0 && act) {
+        const int32_t *Pb = S.Pb() + seg * (Z + 1);
+        int32_t *Pc = S.gPb() + seg * (Z + 2);
+        double *rs = S.gS() + seg * 16;
         bool changed = !(rs[6] == V);
         for (int z = 0; z <= Z; ++z) changed |= Pb[z] != Pc[z];
         Pc[Z + 1] = changed ? 1 : 0;
         if (changed) {
             for (int z = 0; z <= Z; ++z) Pc[z] = Pb[z];
             rs[6] = V;
-            const double Ld = (double)L;
-            const int32_t n0 = S.N0s()[g];
-            double run = 0.0, acc = 0.0;
-            for (int z = 0; z < Z; ++z) {
-                const int w = K.bnd[z + 1] - K.bnd[z];
-                const int Nz = Pb[z + 1] - Pb[z];
-                const double C = __dsub_rn((double)Nz, __ddiv_rn(__dmul_rn((double)n0, (double)w), Ld));
-                const double Q = __dadd_rn(run, __dmul_rn(0.5, C));
-                run = __dadd_rn(run, C);
-                acc = __dadd_rn(acc, __dmul_rn((double)w, Q));
-                S.gQ()[g * Z + z] = Q;
-            }
-            rs[5] = __ddiv_rn(acc, Ld);
         }
     }
     __syncwarp();
-    for (int pi = lane; pi < G * Z; pi += 32) {
-        const int g = pi / Z, z = pi - g * Z;
-        if (g >= nact) continue;
-        double *rs = S.gS() + g * 16;
-        if (S.gPb()[g * (Z + 2) + Z + 1]) {
-            // B1. Eqs. 3-6 in the oracle's operation order, cached until the
-            //     rail's zone counts or V change
-            const double dq = __dsub_rn(S.gQ()[pi], rs[5]);
-            const double dV = __dsub_rn(V, __dmul_rn(K.ka, dq));
-            const double dE = __ddiv_rn(__dmul_rn(dV, K.d), K.t_dev);
-            const double B = exp(__ddiv_rn(-dE, K.kT));
-            const double inv = __ddiv_rn(1.0, __dadd_rn(1.0, B));
-            const double pL = __dmul_rn(K.P0, inv);
-            const double pR = __dmul_rn(pL, B);
-            const double c = __ddiv_rn(__dmul_rn(__dmul_rn(a.alpha, dq), K.d), a.tdev_kT);
-            S.gP()[pi] = make_double2(pR, pL);
-            S.gR1()[pi] = make_double2(pR < 1.0 ? __drcp_rn(__dsub_rn(1.0, pR)) : 0.0,
-                                       pL < 1.0 ? __drcp_rn(__dsub_rn(1.0, pL)) : 0.0);
-            S.gDK()[pi] = make_double2(__dmul_rn(inv, c), -__dmul_rn(__dsub_rn(1.0, inv), c));
+    double Wp = 0.0, Kp = 0.0, Ep = 0.0;
+    if (act && sl < W2) {
+        double *rs = S.gS() + seg * 16;
+        const bool changed = S.gPb()[seg * (Z + 2) + Z + 1] != 0;
+        for (int z = sl; z < Z; z += W2) {
+            const int pi = seg * Z + z;
+            if (changed) {
+                // Q_z - Qbar (S2.1.8) = (Pb_z + Pb_z+1 - F / L) / 2 - D'_z with the
+                // rail's F = sum_z w_z (Pb_z + Pb_z+1) and the per-tile constant D'_z
+                const int32_t *Pb = S.Pb() + seg * (Z + 1);
+                const double h = __dsub_rn((double)(Pb[z] + Pb[z + 1]),
+                                           __dmul_rn((double)S.Fs()[seg], gInvL));
+                const double dq = __fma_rn(0.5, h, -S.gCz()[pi]);
+                const double dV = __fma_rn(-K.ka, dq, V);
+                const double B = exp(__dmul_rn(dV, gXV));            // Eqs. 3-4
+                // 1/(1+B), 1/(1-p_R), 1/(1-p_L) from one division
+                const double x1 = __dadd_rn(1.0, B);
+                const double pL = __ddiv_rn(K.P0, x1);                // Eq. 5
+                const double pR = __dmul_rn(pL, B);                   // Eq. 6
+                const double x2 = __dsub_rn(1.0, pR), x3 = __dsub_rn(1.0, pL);
+                const double x23 = __dmul_rn(x2, x3);
+                const double c = __dmul_rn(gKC, dq);                 // d ln B / d kappa
+                double inv, r1R, r1L;
+                if (x23 > 0.0) {
+                    const double rp = __drcp_rn(__dmul_rn(x1, x23));
+                    inv = __dmul_rn(x23, rp);
+                    r1R = __dmul_rn(__dmul_rn(x1, x3), rp);
+                    r1L = __dmul_rn(__dmul_rn(x1, x2), rp);
+                } else {                                               // a certain trial
+                    inv = __drcp_rn(x1);
+                    r1R = pR < 1.0 ? __drcp_rn(x2) : 0.0;
+                    r1L = pL < 1.0 ? __drcp_rn(x3) : 0.0;
+                }
+                S.gP()[pi] = make_double2(pR, pL);
+                S.gR1()[pi] = make_double2(r1R, r1L);
+                S.gPQ()[pi] = make_double2(__dmul_rn(pR, r1R), __dmul_rn(pL, r1L));
+                S.gDK()[pi] = make_double2(__dmul_rn(inv, c), -__dmul_rn(__dsub_rn(1.0, inv), c));
+                if (open && z == 0) {
+                    const double pin = __dmul_rn(__dmul_rn(K.E_in, inv), B);   // injection into 0
+                    const double pout = __dmul_rn(K.E_out, inv);               // extraction at 0
+                    rs[7] = pin;
+                    rs[8] = pout;
+                    rs[11] = pin < 1.0 ? __drcp_rn(__dsub_rn(1.0, pin)) : 0.0;
+                    rs[12] = pout < 1.0 ? __drcp_rn(__dsub_rn(1.0, pout)) : 0.0;
+                }
+                if (open && z == Z - 1) {
+                    const double pout = __dmul_rn(__dmul_rn(K.E_out, inv), B);  // extraction at L-1
+                    const double pin = __dmul_rn(K.E_in, inv);                  // injection into L-1
+                    rs[9] = pout;
+                    rs[10] = pin;
+                    rs[13] = pout < 1.0 ? __drcp_rn(__dsub_rn(1.0, pout)) : 0.0;
+                    rs[14] = pin < 1.0 ? __drcp_rn(__dsub_rn(1.0, pin)) : 0.0;
+                }
+            }
+            // inner trials of the zone's sites [lo, hi); at an open rail the
+            // outward trials of sites 0 and L-1 are electrode trials, below
+            const int lo = K.bnd[z], hi = K.bnd[z + 1];
+            int nR = 0, nL = 0, aR = 0, aL = 0;
+            for (int w = lo >> 5; w <= (hi - 1) >> 5; ++w) {
+                const int s0 = 32 * w;
+                uint32_t m = FULL;
+                if (lo > s0) m &= FULL << (lo - s0);
+                if (hi < s0 + 32) m &= (1u << (hi - s0)) - 1u;
+                const int idx = seg * LPR * WPL + w;
+                const uint32_t o = S.ow()[idx] & m;
+                uint32_t fR = S.fR()[idx], fL = S.fL()[idx];
+                if (open) {
+                    if (L - 1 >= s0 && L - 1 < s0 + 32) fR &= ~(1u << ((L - 1) - s0));
+                    if (s0 == 0) fL &= ~1u;
+                }
+                nR += __popc(o & fR);
+                nL += __popc(o & fL);
+                aR += __popc(o & fR & S.accR()[idx]);
+                aL += __popc(o & fL & S.accL()[idx]);
+            }
+            if (nR | nL) {
+                const double2 p = S.gP()[pi], r1 = S.gR1()[pi], q = S.gPQ()[pi], dk = S.gDK()[pi];
+                const double wR = trial_weight(aR, nR, p.x, r1.x, q.x);
+                const double wL = trial_weight(aL, nL, p.y, r1.y, q.y);
+                Wp = __dadd_rn(Wp, __dadd_rn(wR, wL));
+                Kp = __fma_rn(wR, dk.x, __fma_rn(wL, dk.y, Kp));
+                Ep = __dadd_rn(Ep, __fma_rn(-(double)nL, p.y, (double)aL));
+                Ep = __dsub_rn(Ep, __fma_rn(-(double)nR, p.x, (double)aR));
+            }
             if (open && z == 0) {
-                const double pin = __dmul_rn(__dmul_rn(K.E_in, inv), B);   // injection into 0
-                const double pout = __dmul_rn(K.E_out, inv);               // extraction at 0
-                rs[7] = pin;
-                rs[8] = pout;
-                rs[11] = pin < 1.0 ? __drcp_rn(__dsub_rn(1.0, pin)) : 0.0;
-                rs[12] = pout < 1.0 ? __drcp_rn(__dsub_rn(1.0, pout)) : 0.0;
+                const double dkR = S.gDK()[pi].x, dkL = S.gDK()[pi].y;
+                const int idx = seg * LPR * WPL;
+                if (S.ow()[idx] & 1u) {        // extraction through the left electrode
+                    const int hit = (S.accL()[idx] & 1u) ? 1 : 0;
+                    Kp = __fma_rn(trial_weight(hit, 1, rs[8], rs[12], __dmul_rn(rs[8], rs[12])), dkL, Kp);
+                    Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[8]));
+                } else {                       // injection into site 0
+                    const int hit = (S.accR()[idx] & 1u) ? 1 : 0;
+                    Kp = __fma_rn(trial_weight(hit, 1, rs[7], rs[11], __dmul_rn(rs[7], rs[11])), dkR, Kp);
+                    Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[7]));
+                }
             }
             if (open && z == Z - 1) {
-                const double pout = __dmul_rn(__dmul_rn(K.E_out, inv), B);  // extraction at L-1
-                const double pin = __dmul_rn(K.E_in, inv);                  // injection into L-1
-                rs[9] = pout;
-                rs[10] = pin;
-                rs[13] = pout < 1.0 ? __drcp_rn(__dsub_rn(1.0, pout)) : 0.0;
-                rs[14] = pin < 1.0 ? __drcp_rn(__dsub_rn(1.0, pin)) : 0.0;
+                const double dkR = S.gDK()[pi].x, dkL = S.gDK()[pi].y;
+                const int idx = seg * LPR * WPL + ((L - 1) >> 5);
+                const uint32_t bit = 1u << ((L - 1) & 31);
+                if (S.ow()[idx] & bit) {       // extraction through the right electrode
+                    const int hit = (S.accR()[idx] & bit) ? 1 : 0;
+                    Kp = __fma_rn(trial_weight(hit, 1, rs[9], rs[13], __dmul_rn(rs[9], rs[13])), dkR, Kp);
+                    Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[9]));
+                } else {                       // injection into site L-1
+                    const int hit = (S.accL()[idx] & bit) ? 1 : 0;
+                    Kp = __fma_rn(trial_weight(hit, 1, rs[10], rs[14], __dmul_rn(rs[10], rs[14])), dkL, Kp);
+                    Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[10]));
+                }
             }
         }
-        // B2. inner trials of the zone's sites [lo, hi); at an open rail the
-        //     outward trials of sites 0 and L-1 are electrode trials, below
-        const int lo = K.bnd[z], hi = K.bnd[z + 1];
-        int nR = 0, nL = 0, aR = 0, aL = 0;
-        for (int w = lo >> 5; w <= (hi - 1) >> 5; ++w) {
-            const int s0 = 32 * w;
-            uint32_t m = FULL;
-            if (lo > s0) m &= FULL << (lo - s0);
-            if (hi < s0 + 32) m &= (1u << (hi - s0)) - 1u;
-            const int idx = g * LPR * WPL + w;
-            const uint32_t o = S.ow()[idx] & m;
-            uint32_t fR = S.fR()[idx], fL = S.fL()[idx];
-            if (open) {
-                if (L - 1 >= s0 && L - 1 < s0 + 32) fR &= ~(1u << ((L - 1) - s0));
-                if (s0 == 0) fL &= ~1u;
-            }
-            nR += __popc(o & fR);
-            nL += __popc(o & fL);
-            aR += __popc(o & fR & S.accR()[idx]);
-            aL += __popc(o & fL & S.accL()[idx]);
-        }
-        const double2 p = S.gP()[pi], r1 = S.gR1()[pi], dk = S.gDK()[pi];
-        const double wR = trial_weight(aR, nR, p.x, r1.x), wL = trial_weight(aL, nL, p.y, r1.y);
-        const double Wz = __dadd_rn(wR, wL);
-        double Kz = __dadd_rn(__dmul_rn(wR, dk.x), __dmul_rn(wL, dk.y));
-        // innovation of the current: left trials (a - p) minus right trials (a - p)
-        double Ez = __dsub_rn(__dsub_rn((double)aL, __dmul_rn((double)nL, p.y)),
-                              __dsub_rn((double)aR, __dmul_rn((double)nR, p.x)));
-        if (open && z == 0) {
-            const int idx = g * LPR * WPL;
-            if (S.ow()[idx] & 1u) {        // extraction through the left electrode
-                const int hit = (S.accL()[idx] & 1u) ? 1 : 0;
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[8], rs[12]), dk.y));
-                Ez = __dadd_rn(Ez, __dsub_rn((double)hit, rs[8]));
-            } else {                       // injection into site 0
-                const int hit = (S.accR()[idx] & 1u) ? 1 : 0;
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[7], rs[11]), dk.x));
-                Ez = __dsub_rn(Ez, __dsub_rn((double)hit, rs[7]));
-            }
-        }
-        if (open && z == Z - 1) {
-            const int idx = g * LPR * WPL + ((L - 1) >> 5);
-            const uint32_t bit = 1u << ((L - 1) & 31);
-            if (S.ow()[idx] & bit) {       // extraction through the right electrode
-                const int hit = (S.accR()[idx] & bit) ? 1 : 0;
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[9], rs[13]), dk.x));
-                Ez = __dsub_rn(Ez, __dsub_rn((double)hit, rs[9]));
-            } else {                       // injection into site L-1
-                const int hit = (S.accL()[idx] & bit) ? 1 : 0;
-                Kz = __dadd_rn(Kz, __dmul_rn(trial_weight(hit, 1, rs[10], rs[14]), dk.y));
-                Ez = __dadd_rn(Ez, __dsub_rn((double)hit, rs[10]));
-            }
-        }
-        S.gWK()[pi] = make_double2(Wz, Kz);
-        S.gEta()[pi] = Ez;
     }
-    __syncwarp();
+    // reduce over the W2 lanes of each rail slot (lane sl == 0 holds the sums)
+    for (int off = W2 >> 1; off >= 1; off >>= 1) {
+        Wp = __dadd_rn(Wp, __shfl_xor_sync(FULL, Wp, off, W2));
+        Kp = __dadd_rn(Kp, __shfl_xor_sync(FULL, Kp, off, W2));
+        Ep = __dadd_rn(Ep, __shfl_xor_sync(FULL, Ep, off, W2));
+    }
+    Ws = Wp;
+    Ks = Kp;
+    Es = Ep;
 }
 
 template <int LPR, int WPL, bool ACC, bool GRAD = false>
@@ -603,7 +625,31 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             S.accL()[i] = 0;
         }
     }
+    // gradient pass: lanes per rail that take zones (a power of two <= LPR)
+    int gW2 = 1;
+    while (gW2 < Z && gW2 < LPR) gW2 <<= 1;
+    // 1 / L; dV_z -> ln B_z = -dV_z d / (t_dev kT) (Eqs. 3-4); dq -> d ln B_z / d kappa
+    double gInvL = 0.0, gXV = 0.0, gKC = 0.0;
     if constexpr (GRAD) {
+        gInvL = 1.0 / (double)L;
+        gXV = -(a.K->d / a.K->t_dev) / a.K->kT;
+        gKC = (a.alpha * a.K->d) / a.tdev_kT;
+        // D'_z = D_z - sum_z' w_z' D_z' / L with D_z = sum_{z'<z} c_z' + c_z / 2,
+        // c_z = N0 w_z / L: the background part of Q_z - Qbar, fixed per rail
+        if (sl == 0) {
+            const int32_t n0 = active ? a.N0[rail] : 0;
+            double run = 0.0, acc = 0.0;
+            for (int z = 0; z < Z; ++z) {
+                const int w = a.bnd[z + 1] - a.bnd[z];
+                const double cz = ((double)n0 * (double)w) / (double)L;
+                const double D = run + 0.5 * cz;
+                run += cz;
+                acc += (double)w * D;
+                S.gCz()[seg * Z + z] = D;
+            }
+            const double mean = acc / (double)L;
+            for (int z = 0; z < Z; ++z) S.gCz()[seg * Z + z] -= mean;
+        }
         if (sl == 0) S.gS()[seg * 16 + 6] = __longlong_as_double(0x7FF8000000000000ll);  // no cache
         if (sl == 0)
             for (int i = 0; i < kGradState; ++i)
@@ -981,36 +1027,28 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             // ---- 5c. gradient pass: score of this step's trials
             if constexpr (GRAD) {
                 __syncwarp();
-                grad_step_score<LPR, WPL>(a, S, t, nact, open, lane);
+                double Ws, Ks, Es;
+                grad_step_score<LPR, WPL>(a, S, t, nact, open, seg, sl, gW2, gInvL, gXV, gKC,
+                                          Ws, Ks, Es);
                 if (sl == 0 && seg < nact) {
                     double *st = S.gS() + seg * 16;      // W, K, G_W, G_K, G_1
-                    double Ws = 0.0, Ks = 0.0, Es = 0.0;
-                    for (int z = 0; z < Z; ++z) {
-                        const double2 wk = S.gWK()[seg * Z + z];
-                        Ws = __dadd_rn(Ws, wk.x);
-                        Ks = __dadd_rn(Ks, wk.y);
-                        Es = __dadd_rn(Es, S.gEta()[seg * Z + z]);
-                    }
-                    if (a.wZ) {
-                        // zone counts at the start of step t pair with the score of steps < t
-                        double fZ = 0.0;
+                    // coefficient of the score before this step: the zone counts at
+                    // the start of step t, less the current's innovation (a control
+                    // variate of zero mean)
+                    double d = 0.0;
+                    if (a.fZa) {
+                        double fZ = -a.fZb[t];
                         for (int z = 0; z < Z; ++z) {
                             const int nz = S.Pb()[seg * (Z + 1) + z + 1] - S.Pb()[seg * (Z + 1) + z];
-                            const long long tot = (long long)a.Zc_tot[(int64_t)t * Z + z];
-                            const double b = a.loo > 0.0 ? __ddiv_rn((double)(tot - nz), a.loo) : 0.0;
-                            fZ = __dadd_rn(fZ, __dmul_rn(a.wZ[(int64_t)t * Z + z], __dsub_rn((double)nz, b)));
+                            fZ = __fma_rn(a.fZa[(int64_t)t * Z + z], (double)nz, fZ);
                         }
-                        st[2] = __dadd_rn(st[2], __dmul_rn(fZ, st[0]));
-                        st[3] = __dadd_rn(st[3], __dmul_rn(fZ, st[1]));
-                        st[4] = __dadd_rn(st[4], fZ);
+                        d = fZ;
                     }
-                    if (a.wJ) {
-                        // control variate: the current's innovation times the score
-                        // before this step has zero mean
-                        const double c = __dmul_rn(a.wJ[t], Es);
-                        st[2] = __dsub_rn(st[2], __dmul_rn(c, st[0]));
-                        st[3] = __dsub_rn(st[3], __dmul_rn(c, st[1]));
-                        st[4] = __dsub_rn(st[4], c);
+                    if (a.wJ) d = __fma_rn(-a.wJ[t], Es, d);
+                    if (d != 0.0) {
+                        st[2] = __fma_rn(d, st[0], st[2]);
+                        st[3] = __fma_rn(d, st[1], st[3]);
+                        st[4] = __dadd_rn(st[4], d);
                     }
                     st[0] = __dadd_rn(st[0], Ws);
                     st[1] = __dadd_rn(st[1], Ks);
@@ -1096,13 +1134,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             if constexpr (GRAD) {
                 // the current of step t pairs with the score of steps <= t
                 if (a.wJ && sl == 0 && seg < nact) {
-                    double *st = S.gS() + seg * 16;
-                    const long long tot = (long long)a.J_tot[t];
-                    const double b = a.loo > 0.0 ? __ddiv_rn((double)(tot - Jrail), a.loo) : 0.0;
-                    const double fJ = __dmul_rn(a.wJ[t], __dsub_rn((double)Jrail, b));
-                    st[2] = __dadd_rn(st[2], __dmul_rn(fJ, st[0]));
-                    st[3] = __dadd_rn(st[3], __dmul_rn(fJ, st[1]));
-                    st[4] = __dadd_rn(st[4], fJ);
+                    const double2 ab = a.fJab[t];
+                    if (ab.x != 0.0 || ab.y != 0.0) {
+                        double *st = S.gS() + seg * 16;
+                        const double fJ = __fma_rn(ab.x, (double)Jrail, -ab.y);
+                        st[2] = __fma_rn(fJ, st[0], st[2]);
+                        st[3] = __fma_rn(fJ, st[1], st[3]);
+                        st[4] = __dadd_rn(st[4], fJ);
+                    }
                 }
             }
             __syncwarp();
