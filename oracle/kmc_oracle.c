@@ -455,6 +455,98 @@ static void rail_step(const orc_params *P, int r, uint32_t t, double V, uint8_t 
     *J_acc += J;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Brick-wall variant (not the paper's rule; an optional alternative).  At   */
+/* step t only the bonds (b, b+1) with b = t (mod 2) are active; the bond    */
+/* (-1, 0) to the left reservoir has b = -1 (odd) and (L-1, L) to the right  */
+/* one b = L-1.  Every site belongs to exactly one active bond, so an ion    */
+/* makes at most one trial per step and no two hops can target one site.   */
+/* An active inner bond holding one ion tries that ion's hop across it with */
+/* the probability and the draw of Eqs. 5-6 (right hop: the right draw of   */
+/* the ion's site, left hop: its left draw); the electrode bonds exchange   */
+/* ions as in the synchronous rule.                                         */
+/* ------------------------------------------------------------------------ */
+static void rail_step_brick(const orc_params *P, int r, uint32_t t, double V, uint8_t *occ,
+                            int32_t N0, const double *P0row, double P0scalar, double E_in,
+                            double E_out, uint8_t *next, int64_t *J_acc, int64_t *zc_acc,
+                            orc_log_entry *log, int64_t cap, int64_t *count)
+{
+    const int L = P->L, Z = P->Z;
+    const int open = P->electrodes == 1;
+    int32_t Nz[ORC_MAX_ZONES];
+    double dV[ORC_MAX_ZONES], B[ORC_MAX_ZONES], inv[ORC_MAX_ZONES];
+    for (int z = 0; z < Z; ++z) Nz[z] = 0;
+    for (int k = 0; k < L; ++k)
+        if (occ[k]) Nz[orc_zone_of(k, L, Z)] += 1;
+    for (int z = 0; z < Z; ++z) zc_acc[z] += Nz[z];
+    orc_zone_field(P, Nz, N0, V, dV, B, inv);
+
+    const int par = (int)(t & 1u);
+    int64_t J = 0;
+    memcpy(next, occ, (size_t)L);
+    for (int b = -1; b <= L - 1; ++b) {
+        if (((b % 2) + 2) % 2 != par) continue;   /* inactive bond this step */
+        double uR, uL, pl, pr;
+        if (b == -1) {                            /* left reservoir | site 0 */
+            if (!open) continue;
+            const int z = orc_zone_of(0, L, Z);
+            site_uniforms(P, 0u, (uint32_t)r, t, &uR, &uL);
+            if (occ[0]) {                         /* extraction: leftward out of site 0 */
+                orc_hop_probs(E_out, B[z], inv[z], &pl, &pr);
+                if (trial(uL, pl, log, cap, count, r, t, 0, 1, 2)) {
+                    next[0] = 0;
+                    J += 1;
+                }
+            } else {                              /* injection: rightward into site 0 */
+                orc_hop_probs(E_in, B[z], inv[z], &pl, &pr);
+                if (trial(uR, pr, log, cap, count, r, t, 0, 0, 1)) {
+                    next[0] = 1;
+                    J -= 1;
+                }
+            }
+        } else if (b == L - 1) {                  /* site L-1 | right reservoir */
+            if (!open) continue;
+            const int k = L - 1;
+            const int z = orc_zone_of(k, L, Z);
+            site_uniforms(P, (uint32_t)k, (uint32_t)r, t, &uR, &uL);
+            if (occ[k]) {                         /* extraction: rightward out of L-1 */
+                orc_hop_probs(E_out, B[z], inv[z], &pl, &pr);
+                if (trial(uR, pr, log, cap, count, r, t, k, 0, 2)) {
+                    next[k] = 0;
+                    J -= 1;
+                }
+            } else {                              /* injection: leftward into L-1 */
+                orc_hop_probs(E_in, B[z], inv[z], &pl, &pr);
+                if (trial(uL, pl, log, cap, count, r, t, k, 1, 1)) {
+                    next[k] = 1;
+                    J += 1;
+                }
+            }
+        } else if (occ[b] && !occ[b + 1]) {       /* the ion at b hops right */
+            const int z = orc_zone_of(b, L, Z);
+            site_uniforms(P, (uint32_t)b, (uint32_t)r, t, &uR, &uL);
+            orc_hop_probs(P0row ? P0row[b] : P0scalar, B[z], inv[z], &pl, &pr);
+            if (trial(uR, pr, log, cap, count, r, t, b, 0, 0)) {
+                next[b] = 0;
+                next[b + 1] = 1;
+                J -= 1;
+            }
+        } else if (!occ[b] && occ[b + 1]) {       /* the ion at b+1 hops left */
+            const int k = b + 1;
+            const int z = orc_zone_of(k, L, Z);
+            site_uniforms(P, (uint32_t)k, (uint32_t)r, t, &uR, &uL);
+            orc_hop_probs(P0row ? P0row[k] : P0scalar, B[z], inv[z], &pl, &pr);
+            if (trial(uL, pl, log, cap, count, r, t, k, 1, 0)) {
+                next[k] = 0;
+                next[b] = 1;
+                J += 1;
+            }
+        }
+    }
+    memcpy(occ, next, (size_t)L);
+    *J_acc += J;
+}
+
 int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, uint8_t *occ,
             const int32_t *N0, const double *P0site, const int32_t *rail_ids, int64_t *J_out,
             int64_t *Zc_out, int64_t *J_rail, orc_log_entry *log, int64_t log_cap,
@@ -462,6 +554,7 @@ int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, u
 {
     const int R = P->R, L = P->L, Z = P->Z;
     if (L < 2 || Z < 1 || Z > ORC_MAX_ZONES || Z > L || R < 0) return -1;
+    if (P->rule != 0 && P->rule != 1) return -1;
     if (t0 < 0 || t0 + n_steps > (int64_t)ORC_INIT_STEP) return -1;
     const double P0scalar = orc_p0(P->nu, P->Ea, P->T, P->dt);
     const double E = -expm1(-(2.0 * P->k_e * P->dt));
@@ -490,9 +583,14 @@ int orc_run(const orc_params *P, const double *V, int64_t t0, int64_t n_steps, u
             for (int r = 0; r < R; ++r) {
                 int64_t Jr = 0;
                 const int rail = rail_ids ? rail_ids[r] : r;
-                rail_step(P, rail, t, V[t], occ + (int64_t)r * L, N0[r],
-                          P0site ? P0site + (int64_t)r * L : NULL, P0scalar, E_in, E_out,
-                          mvR, mvL, next, &Jr, zc, log, log_cap, log_count, NULL);
+                if (P->rule == 1)
+                    rail_step_brick(P, rail, t, V[t], occ + (int64_t)r * L, N0[r],
+                                    P0site ? P0site + (int64_t)r * L : NULL, P0scalar, E_in,
+                                    E_out, next, &Jr, zc, log, log_cap, log_count);
+                else
+                    rail_step(P, rail, t, V[t], occ + (int64_t)r * L, N0[r],
+                              P0site ? P0site + (int64_t)r * L : NULL, P0scalar, E_in, E_out,
+                              mvR, mvL, next, &Jr, zc, log, log_cap, log_count, NULL);
                 J += Jr;
                 if (J_rail) J_rail[r] += Jr;
             }
@@ -526,6 +624,7 @@ int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64
 {
     const int R = P->R, L = P->L, Z = P->Z;
     if (L < 2 || Z < 1 || Z > ORC_MAX_ZONES || Z > L || R < 0) return -1;
+    if (P->rule != 0) return -1;   /* the score hook follows the synchronous rule */
     if (t0 < 0 || t0 + n_steps > (int64_t)ORC_INIT_STEP) return -1;
     if ((wJ && !J_tot) || (wZ && !Zc_tot)) return -1;
     const double P0scalar = orc_p0(P->nu, P->Ea, P->T, P->dt);

@@ -28,7 +28,7 @@ typedef struct {
     double rho_e;       /* reservoir density in [0, 1] */
     uint64_t seed;      /* Philox key */
     uint32_t instance;  /* fourth Philox counter word */
-    int32_t pad;
+    int32_t rule;       /* 0 synchronous update (S2.1.7), 1 brick-wall (even/odd bonds) */
 } orc_params;
 
 typedef struct {

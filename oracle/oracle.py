@@ -32,7 +32,7 @@ class OrcParams(ctypes.Structure):
         ("d", ctypes.c_double), ("dt", ctypes.c_double), ("T", ctypes.c_double),
         ("Ea", ctypes.c_double), ("nu", ctypes.c_double), ("alpha", ctypes.c_double),
         ("kappa", ctypes.c_double), ("k_e", ctypes.c_double), ("rho_e", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32), ("pad", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32), ("rule", ctypes.c_int32),
     ]
 
 
@@ -111,7 +111,8 @@ def params(dev) -> OrcParams:
     return OrcParams(R=d["R"], L=d["L"], Z=d["Z"], electrodes=d["electrodes"], d=d["d"],
                      dt=d["dt"], T=d["T"], Ea=d["Ea"], nu=d["nu"], alpha=d["alpha"],
                      kappa=d["kappa"], k_e=d["k_e"], rho_e=d["rho_e"],
-                     seed=d["seed"] & 0xFFFFFFFFFFFFFFFF, instance=d["instance"], pad=0)
+                     seed=d["seed"] & 0xFFFFFFFFFFFFFFFF, instance=d["instance"],
+                     rule=d.get("rule", 0))
 
 
 # ------------------------------------------------------------- primitives

@@ -136,3 +136,63 @@ def stationary(T):
     pi = np.real(v[:, i])
     pi = pi / pi.sum()
     return pi
+
+
+def transition_matrix_brick(dev, V, N0, parity, Ea_site=None):
+    """Exact one-step transition matrix of the brick-wall variant at a step of
+    the given parity: only bonds (b, b+1) with b = parity (mod 2) are active,
+    b = -1 being the left reservoir's bond and b = L-1 the right one's.  An
+    active bond holding exactly one ion tries that ion's hop across it; the
+    trials of different bonds touch disjoint sites, so every joint outcome
+    maps to a configuration directly (no exclusion conflicts exist)."""
+    L, Z = dev["L"], dev["Z"]
+    open_ = dev["electrodes"] == 1
+    kT = KB * dev["T"]
+
+    def base_prob(Ea):
+        return 1.0 - math.exp(-2.0 * dev["nu"] * math.exp(-Ea / kT) * dev["dt"])
+
+    P0 = [base_prob(e) for e in Ea_site] if Ea_site is not None else [base_prob(dev["Ea"])] * L
+    E = 1.0 - math.exp(-2.0 * dev["k_e"] * dev["dt"])
+    E_in, E_out = E * dev["rho_e"], E * (1.0 - dev["rho_e"])
+    n = 1 << L
+    T = np.zeros((n, n))
+    for s in range(n):
+        occ = [(s >> k) & 1 for k in range(L)]
+        B, zones = field_B(occ, L, Z, N0, V, dev)
+
+        def right(k):   # Boltzmann share of a rightward hop in the zone of site k
+            return B[zones[k]] / (1.0 + B[zones[k]])
+
+        def left(k):
+            return 1.0 / (1.0 + B[zones[k]])
+
+        # (probability, site that empties or -1, site that fills or -1)
+        trials = []
+        for b in range(-1, L):
+            if b % 2 != parity % 2:
+                continue
+            if b == -1:
+                if open_:
+                    trials.append((E_out * left(0), 0, -1) if occ[0] else (E_in * right(0), -1, 0))
+            elif b == L - 1:
+                if open_:
+                    trials.append((E_out * right(L - 1), L - 1, -1) if occ[L - 1]
+                                  else (E_in * left(L - 1), -1, L - 1))
+            elif occ[b] and not occ[b + 1]:
+                trials.append((P0[b] * right(b), b, b + 1))
+            elif occ[b + 1] and not occ[b]:
+                trials.append((P0[b + 1] * left(b + 1), b + 1, b))
+        for outcome in itertools.product((0, 1), repeat=len(trials)):
+            prob = 1.0
+            nxt = list(occ)
+            for (p, src, dst), hit in zip(trials, outcome):
+                prob *= p if hit else 1.0 - p
+                if hit:
+                    if src >= 0:
+                        nxt[src] = 0
+                    if dst >= 0:
+                        nxt[dst] = 1
+            if prob > 0.0:
+                T[s, sum(v << k for k, v in enumerate(nxt))] += prob
+    return T
