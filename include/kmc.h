@@ -65,6 +65,12 @@ typedef struct kmc_params {
                                  1: Bernoulli(fill) per site; 2: caller occupancy            */
     int64_t n_ions;           /* init_mode 0                                                 */
     double fill;              /* init_mode 1                                                 */
+    int32_t update_rule;      /* 0: the paper's synchronous update (S2.1.6-S2.1.7);
+                                 1: brick-wall variant, not in the paper: at step t only
+                                 bonds (b, b+1) with b = t mod 2 are active (the left
+                                 electrode's bond is b = -1), each ion makes at most one
+                                 trial, across its active bond, and no hops conflict    */
+    int32_t reserved;         /* 0                                                           */
 } kmc_params;
 
 /* One decision whose uniform fell within 1e-12 of its threshold. */

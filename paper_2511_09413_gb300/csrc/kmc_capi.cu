@@ -80,6 +80,8 @@ int validate(const kmc_params *p, const double *V, int64_t n_total, const uint8_
         if (!(p->rho_electrode >= 0.0 && p->rho_electrode <= 1.0))
             return fail(KMC_E_ARG, "rho_electrode must be in [0, 1]");
     }
+    if (p->update_rule != 0 && p->update_rule != 1)
+        return fail(KMC_E_ARG, "update_rule must be 0 or 1 (got %d)", p->update_rule);
     if (n_total < 0 || n_total >= (int64_t)kInitStep)
         return fail(KMC_E_ARG, "n_steps_total must be in [0, 2^32 - 1)");
     if (n_total > 0 && !V) return fail(KMC_E_ARG, "V_per_step is NULL");
@@ -190,6 +192,7 @@ void fill_args(kmc_handle *h)
     a.inv_LkT = (float)(1.0 / ((double)L * kT));
     a.ka_f = (float)(p.kappa * p.alpha_V);
     a.delta = 1.0f / 1024.0f;
+    a.rule = p.update_rule;
 }
 
 int init_exact_count(kmc_handle *h)
@@ -483,6 +486,8 @@ int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, dou
     if (!h || !grad_out) return fail(KMC_E_ARG, "handle or grad_out is NULL");
     if (h->P0site)
         return fail(KMC_E_ARG, "kmc_grad needs a scalar barrier (the handle has per-site Ea)");
+    if (h->p.update_rule != 0)
+        return fail(KMC_E_ARG, "kmc_grad follows the synchronous update (update_rule 0)");
     const kmc_params &p = h->p;
     const int64_t R = p.n_rails, L = p.n_sites, Z = p.n_zones, n = h->t;
     const bool has_rho = p.init_mode == 1 && p.fill > 0.0 && p.fill < 1.0;

@@ -62,6 +62,7 @@ struct SweepArgs {
     float delta;                  // relative half-width of the FP32 probability band
     float P0f_scalar;             // scalar P0 in FP32 (host copy of DevConst::P0f)
     float E_inf, E_outf;          // electrode base probabilities in FP32
+    int32_t rule;                 // 0 synchronous update, 1 brick-wall (even/odd bonds)
 
     // likelihood-ratio gradient pass only (unused by the forward sweep)
     // With the forward's totals J_t, Zc_t and the leave-one-out divisor R - 1,

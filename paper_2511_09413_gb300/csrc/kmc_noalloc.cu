@@ -95,6 +95,7 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     if (p->n_zones < 1 || p->n_zones > KMC_MAX_ZONES || p->n_zones > p->n_sites)
         return fail(KMC_E_ARG, "n_zones must be in [1, min(n_sites, 32)]");
     if (p->electrodes != 0 && p->electrodes != 1) return fail(KMC_E_ARG, "electrodes must be 0 or 1");
+    if (p->update_rule != 0 && p->update_rule != 1) return fail(KMC_E_ARG, "update_rule must be 0 or 1");
     if (!finite_pos(p->site_spacing_nm) || !finite_pos(p->dt_s) || !finite_pos(p->T_K))
         return fail(KMC_E_ARG, "site_spacing_nm, dt_s and T_K must be > 0");
     if (!(isfinite(p->nu_Hz) && p->nu_Hz >= 0.0) || !isfinite(p->Ea_eV) || !isfinite(p->alpha_V) ||
@@ -196,6 +197,7 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     a.inv_LkT = (float)(1.0 / ((double)L * kT));
     a.ka_f = (float)(p->kappa * p->alpha_V);
     a.delta = 1.0f / 1024.0f;
+    a.rule = p->update_rule;
     // FP32 images of the base probabilities; the band factors absorb their rounding
     a.P0f_scalar = (float)P0;
     a.E_inf = (float)E_in;

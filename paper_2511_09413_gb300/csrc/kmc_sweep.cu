@@ -275,8 +275,11 @@ __device__ __forceinline__ Decision decide(const WarpSmem<LPR, WPL> &S, const Sw
     D.idx = g2 * LPR * WPL + (site >> 5);
     D.bit = 1u << (site & 31);
     D.occd = (S.ow()[D.idx] & D.bit) != 0;
-    const bool tryR = D.occd ? (S.fR()[D.idx] & D.bit) != 0 : (isE && site == 0);
-    const bool tryL = D.occd ? (S.fL()[D.idx] & D.bit) != 0 : (isE && site == L - 1);
+    // an occupied site tries a direction whose neighbour (or open electrode) is
+    // free; at an empty electrode site the same mask bits say whether an
+    // injection is tried (set when the masks are built)
+    const bool tryR = (S.fR()[D.idx] & D.bit) != 0;
+    const bool tryL = (S.fL()[D.idx] & D.bit) != 0;
     const float2 bi = S.zf()[g2 * Z + z];          // (B, 1/(1+B)); (0, 0) when undecidable
     const bool ok = bi.y > 0.0f;
     const float sR = bi.y * bi.x, sL = bi.y;
@@ -714,7 +717,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             const uint32_t t = (uint32_t)(t0 + s);
             int32_t *tr = trace + (s - c0) * (1 + Z);
 
-            if (dirty) {
+            // the brick-wall rule's active bonds alternate: its candidates change
+            // every step even when the occupancy does not
+            if (dirty || a.rule != 0) {
                 // ---- 1. zone counts: segmented scan of popcounts
                 int cnt = 0;
 #pragma unroll
@@ -767,9 +772,25 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                                                   : (sl > 0 ? (f_prev >> 31) : (open ? 1u : 0u));
                         const uint32_t cn = j < WPL - 1 ? (f[j < WPL - 1 ? j + 1 : 0] & 1u)
                                                         : (sl < LPR - 1 ? (f_next & 1u) : 0u);
-                        const uint32_t fL = (f[j] << 1) | cp;
+                        uint32_t fL = (f[j] << 1) | cp;
                         uint32_t fR = (f[j] >> 1) | (cn << 31);
                         if (open) fR |= lastm[j];
+                        // brick-wall rule: only bonds (b, b+1) with b = t (mod 2) are
+                        // active; a site of the parity of t faces its active bond on
+                        // the right, the others on the left (site parity = bit parity)
+                        bool inj0 = open, injL = open;
+                        if (a.rule != 0) {
+                            const uint32_t rmask = (t & 1u) ? 0xAAAAAAAAu : 0x55555555u;
+                            fR &= rmask;
+                            fL &= ~rmask;
+                            inj0 = open && (t & 1u);                       // bond -1 active
+                            injL = open && (((uint32_t)(L - 1) ^ t) & 1u) == 0u;  // bond L-1
+                        }
+                        // empty electrode sites: the right bit of site 0 and the left bit
+                        // of site L-1 mark an injection trial, the other bits are clear
+                        const uint32_t e0 = firstm[j] & ~o[j], eL = lastm[j] & ~o[j];
+                        fR = (fR & ~(e0 | eL)) | (inj0 ? e0 : 0u);
+                        fL = (fL & ~(e0 | eL)) | (injL ? eL : 0u);
                         const int wi = seg * LPR * WPL + wbase + j;
                         S.fR()[wi] = fR;
                         S.fL()[wi] = fL;

@@ -47,6 +47,7 @@ class kmc_params(ctypes.Structure):
         ("rho_electrode", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32), ("init_mode", ctypes.c_int32),
         ("n_ions", ctypes.c_int64), ("fill", ctypes.c_double),
+        ("update_rule", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -261,7 +262,8 @@ def params_from_device(dev, init_mode: int, n_ions: int = 0, fill: float = 0.0) 
                       nu_Hz=d["nu"], alpha_V=d["alpha"], kappa=d["kappa"],
                       k_electrode_Hz=d["k_e"], rho_electrode=d["rho_e"],
                       seed=d["seed"] & 0xFFFFFFFFFFFFFFFF, instance=d["instance"],
-                      init_mode=init_mode, n_ions=n_ions, fill=fill)
+                      init_mode=init_mode, n_ions=n_ions, fill=fill,
+                      update_rule=d.get("rule", 0), reserved=0)
 
 
 _torch_alloc_cb = None

@@ -45,6 +45,7 @@ class Device:
     rho_e: float = 0.0
     seed: int = 0
     instance: int = 0
+    rule: int = 0          # 0 synchronous update, 1 brick-wall (even/odd bonds)
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)

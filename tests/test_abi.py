@@ -44,9 +44,10 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_struct_layouts_match_header(lib):
     from paper_2511_09413_gb300 import kmc
-    # kmc_params: 4 int32, 9 double, uint64, uint32, int32, int64, double
-    assert ctypes.sizeof(kmc.kmc_params) == 4 * 4 + 9 * 8 + 8 + 4 + 4 + 8 + 8
+    # kmc_params: 4 int32, 9 double, uint64, uint32, int32, int64, double, int32, int32
+    assert ctypes.sizeof(kmc.kmc_params) == 4 * 4 + 9 * 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4
     assert kmc.kmc_params.seed.offset == 16 + 72
+    assert kmc.kmc_params.update_rule.offset == 16 + 72 + 8 + 4 + 4 + 8 + 8
     assert ctypes.sizeof(kmc.kmc_log_entry) == 32
     assert kmc.LOG_DTYPE.itemsize == 32
 
@@ -65,7 +66,8 @@ def _params(**kw):
     dict(n_sites=8, n_zones=9), dict(electrodes=2), dict(dt_s=0.0), dict(T_K=-1.0),
     dict(site_spacing_nm=float("nan")), dict(nu_Hz=-1.0), dict(init_mode=3),
     dict(init_mode=1, fill=1.5), dict(init_mode=0, n_ions=401), dict(init_mode=2),
-    dict(electrodes=1, rho_electrode=1.5), dict(kappa=float("inf")),
+    dict(electrodes=1, rho_electrode=1.5), dict(kappa=float("inf")), dict(update_rule=2),
+    dict(update_rule=-1),
 ])
 def test_validation_rejects_bad_parameters_on_host(lib, bad):
     from paper_2511_09413_gb300 import kmc

@@ -109,3 +109,16 @@ def test_batch_rejects_mixed_seeds(kmc):
     devs[1]["seed"] = 78
     with pytest.raises(kmc.KmcError):
         kmc.Batch(devs, Vs, [2, 2], occ0s=occs)
+
+
+def test_batch_with_brick_wall_devices(kmc):
+    """Devices of either update rule in one batch, each equal to the oracle."""
+    n_steps = 240
+    devs, Vs, occs = _batch_case(10, n_steps, seed=6)
+    for i in range(0, len(devs), 2):
+        devs[i]["rule"] = 1
+    b = kmc.Batch(devs, Vs, [2] * len(devs), occ0s=occs)
+    b.set_launch(8, 64)
+    b.step_n(n_steps)
+    _check_against_oracle(b, devs, Vs, occs, n_steps)
+    b.close()

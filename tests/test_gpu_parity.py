@@ -230,3 +230,35 @@ def test_rapidly_varying_bias_bit_exact(kmc, L, electrodes):
     V = rng.uniform(-4.0, 4.0, size=300)
     V[::7] = 0.0
     _compare(kmc, dev, V, occ0)
+
+
+@pytest.mark.parametrize("L,electrodes,per_site,dt", [
+    (2, 1, False, 5e-7), (3, 0, False, 5e-7), (31, 1, False, 5e-7), (33, 1, True, 5e-7),
+    (100, 0, False, 1e-9), (100, 1, False, 5e-6), (512, 1, True, 5e-7), (1024, 1, False, 5e-7),
+    (1500, 0, True, 5e-7), (2048, 1, False, 5e-6)])
+def test_brick_wall_rule_bit_exact(kmc, L, electrodes, per_site, dt):
+    """The brick-wall variant (even/odd bonds) against the oracle's, with both
+    accept paths and chunked launches."""
+    R = 20
+    dev = _dev(R=R, L=L, Z=min(10, L), dt=dt, electrodes=electrodes,
+               k_e=1e6 if electrodes else 0.0, rho_e=0.3 if electrodes else 0.0, rule=1)
+    occ0 = W.random_occupancy(R, L, 0.3, seed=L + 5)
+    Ea = W.normal_barriers(R, L, 0.40, 0.02, seed=L + 1) if per_site else None
+    V = W.triangle_protocol(3.0, 90, 2)
+    res = [_compare(kmc, dev, V, occ0, Ea=Ea, accept=m, chunks=[7, 53, len(V) - 60])
+           for m in (0, 1)]
+    for x, y in zip(res[0][:3], res[1][:3]):
+        assert np.array_equal(x, y)
+    # the two rules differ on the same draws
+    sync = _compare(kmc, dict(dev, rule=0), V, occ0, Ea=Ea)
+    assert not np.array_equal(sync[2], res[0][2])
+
+
+def test_brick_wall_rule_rejected_by_gradient_pass(kmc):
+    dev = _dev(R=4, L=30, Z=3, rule=1)
+    V = np.zeros(10)
+    sim = kmc.Sim(dev, V, init_mode=1, fill=0.3)
+    sim.step_n(10)
+    with pytest.raises(kmc.KmcError):
+        sim.grad(np.ones(10), None)
+    sim.close()
