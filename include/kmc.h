@@ -230,6 +230,12 @@ int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_
  * when faster.  kmc_batch_accept_path returns the mode in effect. */
 int kmc_batch_set_accept_path(kmc_batch *b, int32_t mode);
 int kmc_batch_accept_path(const kmc_batch *b);
+/* Likelihood-ratio gradient for device inst of the batch over the steps the
+ * batch has simulated: as kmc_grad on that device (same arguments, same
+ * estimator; the device's trajectory is replayed from its own initial
+ * occupancy).  Synchronizes the batch's stream. */
+int kmc_batch_grad(kmc_batch *b, int32_t inst, const double *dLoss_dJ, const double *dLoss_dZc,
+                   double grad_out[4], double stderr_out[4]);
 int64_t kmc_batch_current_step(const kmc_batch *b);
 void kmc_batch_destroy(kmc_batch *b);
 

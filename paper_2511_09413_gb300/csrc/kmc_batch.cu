@@ -417,6 +417,16 @@ int kmc_batch_set_accept_path(kmc_batch *b, int32_t mode)
 
 int kmc_batch_accept_path(const kmc_batch *b) { return b ? b->acc : -1; }
 
+int kmc_batch_grad(kmc_batch *b, int32_t inst, const double *dLoss_dJ, const double *dLoss_dZc,
+                   double grad_out[4], double stderr_out[4])
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (inst < 0 || inst >= (int32_t)b->dev.size()) return fail(KMC_E_ARG, "device index out of range");
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    return kmc_grad(b->dev[inst], dLoss_dJ, dLoss_dZc, grad_out, stderr_out);
+}
+
 int64_t kmc_batch_current_step(const kmc_batch *b) { return b ? b->t : -1; }
 
 void kmc_batch_destroy(kmc_batch *b)

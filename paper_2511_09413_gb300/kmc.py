@@ -72,7 +72,8 @@ EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "
            "kmc_destroy", "kmc_last_error", "kmc_sweep_noalloc", "kmc_batch_create",
            "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
            "kmc_batch_current_step", "kmc_batch_destroy", "kmc_set_accept_path",
-           "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path", "kmc_grad"]
+           "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path", "kmc_grad",
+           "kmc_batch_grad"]
 
 _lib = None
 
@@ -118,6 +119,9 @@ def load(path: str = LIB_PATH):
     L.kmc_batch_destroy.restype = None
     L.kmc_grad.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                            P(ctypes.c_double)]
+    L.kmc_batch_grad.argtypes = [vp, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double),
+                                 P(ctypes.c_double), P(ctypes.c_double)]
+    L.kmc_batch_grad.restype = ctypes.c_int
     L.kmc_set_accept_path.argtypes = [vp, ctypes.c_int]
     L.kmc_accept_path.argtypes = [vp]
     L.kmc_batch_set_accept_path.argtypes = [vp, ctypes.c_int32]
@@ -407,6 +411,23 @@ def kmc_batch_accept_path(b: int) -> int:
     return int(load().kmc_batch_accept_path(ctypes.c_void_p(b)))
 
 
+def kmc_batch_grad(b: int, inst: int, n: int, Z: int, dLoss_dJ: Optional[np.ndarray] = None,
+                   dLoss_dZc: Optional[np.ndarray] = None):
+    """(grad[4], stderr[4]) for device inst of a batch, as kmc_grad."""
+    wJ = None if dLoss_dJ is None else np.ascontiguousarray(dLoss_dJ, dtype=np.float64)
+    wZ = None if dLoss_dZc is None else np.ascontiguousarray(dLoss_dZc, dtype=np.float64)
+    if wJ is not None and wJ.shape != (n,):
+        raise ValueError("dLoss_dJ must have shape (%d,)" % n)
+    if wZ is not None and wZ.shape != (n, Z):
+        raise ValueError("dLoss_dZc must have shape (%d, %d)" % (n, Z))
+    g = np.zeros(4)
+    se = np.zeros(4)
+    _check(load().kmc_batch_grad(ctypes.c_void_p(b), int(inst), _ptr(wJ, ctypes.c_double),
+                                 _ptr(wZ, ctypes.c_double), _ptr(g, ctypes.c_double),
+                                 _ptr(se, ctypes.c_double)))
+    return g, se
+
+
 def kmc_batch_current_step(b: int) -> int:
     return int(load().kmc_batch_current_step(ctypes.c_void_p(b)))
 
@@ -446,6 +467,12 @@ class Batch:
 
     def set_accept_path(self, mode: int = -1):
         kmc_batch_set_accept_path(self.h, mode)
+
+    def grad(self, inst: int, dLoss_dJ: Optional[np.ndarray] = None,
+             dLoss_dZc: Optional[np.ndarray] = None):
+        """Likelihood-ratio gradient of device inst (kmc_batch_grad)."""
+        R, L, Z = self.shapes[inst]
+        return kmc_batch_grad(self.h, inst, self.t, Z, dLoss_dJ, dLoss_dZc)
 
     @property
     def accept_path(self) -> int:

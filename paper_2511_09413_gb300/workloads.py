@@ -190,3 +190,35 @@ def adjoint_relaxation(replicas: int = 256, rails: int = 4096, L: int = 512, fil
     return Workload("adjoint_relaxation_%dx%dx%d" % (replicas, rails, L), dev,
                     relaxation_protocol(n_write, V_write, n_write + n_relax, 0.0),
                     init_mode=1, fill=fill)
+
+
+def potentiation_protocol(n_pulses: int, forget_steps: int, V_pulse: float = 0.8,
+                          pulse_ms: float = 0.5, gap_ms: float = 0.5,
+                          steps_per_ms: int = 2000) -> np.ndarray:
+    """Learning then forgetting: n_pulses pulses of V_pulse lasting pulse_ms,
+    each followed by gap_ms at 0 V, then forget_steps steps at 0 V."""
+    on = int(round(pulse_ms * steps_per_ms))
+    off = int(round(gap_ms * steps_per_ms))
+    period = np.concatenate([np.full(on, float(V_pulse)), np.zeros(off)])
+    return np.concatenate([np.tile(period, n_pulses), np.zeros(forget_steps)])
+
+
+def fit_batch(n_dev: int = 256, seed: int = 11, n_pulses: int = 100, forget_steps: int = 100000,
+              steps_per_ms: int = 2000, sample_every: int = 500):
+    """Devices of the material fit: rails log-uniform in [2,048, 8,192], sites
+    log-uniform in [256, 1,024], filling U(0.1, 0.3), Ea = 0.40 eV, coupling 1,
+    blocking electrodes, dt = 1 ms / steps_per_ms, all driven by the same
+    potentiation protocol (n_pulses pulses of 0.8 V, 0.5 ms, 0.5 ms apart,
+    then forget_steps steps at 0 V).  Returns (devices, V, fills, sample_steps):
+    the learning/forgetting curve is sampled every sample_every steps."""
+    rng = np.random.default_rng(seed)
+    V = potentiation_protocol(n_pulses, forget_steps, steps_per_ms=steps_per_ms)
+    devs, fills = [], []
+    for i in range(n_dev):
+        R = int(round(np.exp(rng.uniform(np.log(2048), np.log(8192)))))
+        L = int(round(np.exp(rng.uniform(np.log(256), np.log(1024)))))
+        fills.append(float(rng.uniform(0.1, 0.3)))
+        devs.append(Device(R=R, L=L, Z=10, electrodes=0, dt=1e-3 / steps_per_ms, seed=seed,
+                           instance=i))
+    sample_steps = np.arange(sample_every - 1, len(V), sample_every, dtype=np.int64)
+    return devs, V, fills, sample_steps

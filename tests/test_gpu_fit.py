@@ -1,0 +1,64 @@
+"""GPU tests of the batched gradient (kmc_batch_grad) and of the material
+fit driven by it: a device's gradient in a batch equals its gradient alone,
+and gradient descent from (0.40 eV, 1.0) moves toward the hidden parameters
+of target curves that the oracle produced."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_09413_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kmc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_09413_gb300 import build, kmc as K
+    build.build()
+    K.load()
+    torch.cuda.init()
+    return K
+
+
+def test_batch_gradient_equals_single_device_gradient(kmc):
+    devs, V, fills, samples = W.fit_batch(5, seed=3, n_pulses=2, forget_steps=1000)
+    devs = [dataclasses.replace(d, R=d.R // 16, L=d.L // 4) for d in devs]
+    n = len(V)
+    b = kmc.Batch(devs, [V] * len(devs), [1] * len(devs), fills=fills)
+    b.set_launch(4, 256)
+    b.step_n(n)
+    rng = np.random.default_rng(0)
+    for i, d in enumerate(devs):
+        wJ = rng.normal(size=n)
+        wZ = rng.normal(size=(n, d.Z))
+        gb, sb = b.grad(i, wJ, wZ)
+        sim = kmc.Sim(d, V, init_mode=1, fill=fills[i])
+        sim.step_n(n)
+        gs, ss = sim.grad(wJ, wZ)
+        sim.close()
+        assert np.array_equal(gb, gs) and np.array_equal(sb, ss), i
+    b.close()
+
+
+def test_fit_moves_toward_hidden_parameters(kmc):
+    from paper_2511_09413_gb300.fit import MaterialFit
+    devs, V, fills, samples = W.fit_batch(4, seed=5, n_pulses=4, forget_steps=4000,
+                                          sample_every=250)
+    devs = [dataclasses.replace(d, R=256, L=160) for d in devs]
+    n = int(samples.max()) + 1
+    target = np.zeros((len(devs), len(samples)))
+    for i, (d, fill) in enumerate(zip(devs, fills)):
+        dev = dict(d.as_dict(), Ea=0.42, kappa=0.9)
+        occ0 = oracle.init_occupancy(dev, 1, fill=fill)
+        _, Zc = oracle.OracleSim(dev, V, occ0).step_n(n)
+        target[i] = Zc[samples, 0] / occ0.sum()
+    fit = MaterialFit(devs, V, fills, samples, target, warps=4, steps_per_launch=512)
+    hist = fit.run(0.40, 1.0, iters=6, lr=(6e-3, 5e-2))
+    assert hist[0].grad[0] < 0          # the loss falls as Ea rises toward 0.42
+    assert abs(hist[-1].Ea - 0.42) < 0.5 * abs(hist[0].Ea - 0.42), [h.Ea for h in hist]
+    assert hist[-1].loss < 0.5 * hist[0].loss, [h.loss for h in hist]
