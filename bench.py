@@ -501,13 +501,72 @@ def run_adjoint(args):
     return 0
 
 
+def run_fit(args):
+    """Batched + adjoint fit: gradient descent on (Ea, kappa) for 256 devices
+    of 2,048-8,192 rails x 256-1,024 sites under a potentiation/forgetting
+    protocol, toward the oracle's curves at the hidden (0.42 eV, 0.9) stored
+    in tests/golden.  Each iteration is one batched forward run and one
+    backward pass per device."""
+    import torch
+    from paper_2511_09413_gb300 import kmc
+    from paper_2511_09413_gb300.fit import MaterialFit
+
+    torch.cuda.set_device(0)
+    kmc.load()
+    name = os.path.join(ROOT, "tests", "golden", "fit_target_%ddev_%dp_%df.npz" % (
+        args.fit_devices, args.fit_pulses, args.fit_forget))
+    tgt = np.load(name)
+    devs, V, fills, samples = W.fit_batch(args.fit_devices, n_pulses=args.fit_pulses,
+                                          forget_steps=args.fit_forget)
+    assert np.array_equal(samples, tgt["sample_steps"])
+    fit = MaterialFit(devs, V, fills, samples, tgt["target"],
+                      stream=torch.cuda.current_stream().cuda_stream)
+    hist = fit.run(0.40, 1.0, iters=args.fit_iters, lr=(6e-3, 5e-2))
+    su = sum(d.R * d.L for d in devs) * fit.n_steps
+    t_f = sum(h.seconds_forward for h in hist)
+    t_b = sum(h.seconds_backward for h in hist)
+    last = hist[-1]
+    Ea_h, k_h = float(tgt["Ea"]), float(tgt["kappa"])
+    line = {
+        "metric": METRIC + ", batched + adjoint fit", "value": su * len(hist) / (t_f + t_b),
+        "unit": UNIT, "n_gpus": 1, "steps": len(hist), "warmup": 0,
+        "ms_per_step": 1e3 * (t_f + t_b) / len(hist), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fit_batch", "devices": len(devs),
+                   "sites_total": sum(d.R * d.L for d in devs),
+                   "protocol": "%d pulses of 0.8 V x 0.5 ms, 0.5 ms apart, then %d steps" % (
+                       args.fit_pulses, args.fit_forget),
+                   "time_steps": fit.n_steps, "samples_per_curve": len(samples),
+                   "target": os.path.relpath(name, ROOT) + " (oracle, %d rails per device)" % int(
+                       tgt["rails_per_device"]),
+                   "hidden": {"Ea": Ea_h, "kappa": k_h},
+                   "value_basis": "forward site-updates per evaluation / (forward + backward time)"},
+        "forward_site_updates_per_s": su * len(hist) / t_f,
+        "backward_site_updates_per_s": su * len(hist) / t_b,
+        "history": [{"Ea": h.Ea, "kappa": h.kappa, "loss": h.loss,
+                     "grad": h.grad.tolist(), "grad_stderr": h.stderr.tolist(),
+                     "s_forward": h.seconds_forward, "s_backward": h.seconds_backward}
+                    for h in hist],
+        "final": {"Ea": last.Ea, "kappa": last.kappa,
+                  "Ea_rel_error": abs(last.Ea - Ea_h) / Ea_h,
+                  "kappa_rel_error": abs(last.kappa - k_h) / k_h},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kmc", "reference"], default="kmc")
-    ap.add_argument("--workload", choices=["hysteresis", "batched", "adjoint"], default="hysteresis")
+    ap.add_argument("--workload", choices=["hysteresis", "batched", "adjoint", "fit"],
+                    default="hysteresis")
+    ap.add_argument("--fit-devices", type=int, default=256)
+    ap.add_argument("--fit-pulses", type=int, default=8)
+    ap.add_argument("--fit-forget", type=int, default=8000)
+    ap.add_argument("--fit-iters", type=int, default=5)
     ap.add_argument("--replicas", type=int, default=256, help="replicas in the adjoint workload")
     ap.add_argument("--adj-write", type=int, default=10000, help="write-pulse steps (adjoint)")
     ap.add_argument("--adj-relax", type=int, default=50000, help="relaxation steps (adjoint)")
@@ -530,6 +589,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "fit":
+        return run_fit(args)
     return run_kmc(args)
 
 
