@@ -131,7 +131,9 @@ struct Layout {
         return align16((size_t)(acc ? 16 : 8) * G * (Z + 2));
     }
     __host__ __device__ static size_t gz8(int Z) { return align16((size_t)8 * G * Z); }
-    __host__ __device__ static size_t pb_bytes(int Z) { return align16((size_t)4 * G * (Z + 1)); }
+    // Pb int [G][Z+1], then the zone counts last written to the trace int [G][Z]
+    __host__ __device__ static size_t pb_only(int Z) { return align16((size_t)4 * G * (Z + 1)); }
+    __host__ __device__ static size_t pb_bytes(int Z) { return pb_only(Z) + align16((size_t)4 * G * Z); }
     __host__ __device__ static size_t bytes(int Z, bool persite, bool acc)
     {
         return FIXED + rm_bytes(Z, acc) + 2 * gz8(Z) + pb_bytes(Z) +
@@ -158,6 +160,7 @@ struct WarpSmem {
     uint32_t rz;    // Layout::rm_bytes(Z, acc)
     uint32_t gz;    // Layout::gz8(Z)
     uint32_t pbz;   // Layout::pb_bytes(Z)
+    uint32_t npo;   // offset of the zone counts last written to the trace
     uint32_t goff;  // Layout::bytes(Z, persite, acc): start of the gradient-pass region
     uint32_t gzq;   // align16(8 G Z)
     __device__ uint32_t *mvR() const { return (uint32_t *)(b + Ly::MVR); }
@@ -180,6 +183,7 @@ struct WarpSmem {
     __device__ float2 *P0b() const { return (float2 *)(b + Ly::FIXED + rz + gz); }
     __device__ int32_t *Pb() const { return (int32_t *)(b + Ly::FIXED + rz + 2 * gz); }
     __device__ float *P0f() const { return (float *)(b + Ly::FIXED + rz + 2 * gz + pbz); }
+    __device__ int32_t *Np() const { return (int32_t *)(b + npo); }
     __device__ uint32_t *accR() const { return (uint32_t *)(b + goff); }
     __device__ uint32_t *accL() const { return (uint32_t *)(b + goff + align16(4 * Ly::W)); }
     __device__ uint8_t *gbase() const { return b + goff + 2 * align16(4 * Ly::W); }
@@ -606,6 +610,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     S.rz = (uint32_t)Ly::rm_bytes(Z, ACC);
     S.gz = (uint32_t)Ly::gz8(Z);
     S.pbz = (uint32_t)Ly::pb_bytes(Z);
+    S.npo = (uint32_t)(Ly::FIXED + S.rz + 2 * S.gz + Ly::pb_only(Z));
     S.goff = (uint32_t)wb0;
     S.gzq = (uint32_t)align16((size_t)8 * G * Z);
     // the gradient pass writes no traces: no trace buffer
@@ -620,6 +625,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         zone_tab[k] = (uint8_t)z;
     }
     for (int i = threadIdx.x; i < trace_len; i += blockDim.x) trace[i] = 0;
+    for (int pi = lane; pi < G * Z; pi += 32) S.Np()[pi] = 0;
     for (int i = lane; i < 32 * WPL; i += 32) {
         S.mvR()[i] = 0;
         S.mvL()[i] = 0;
@@ -711,6 +717,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     unsigned n_draw = 0, n_move = 0;
     __syncthreads();
 
+    int zrun = 0;   // flush: this CTA's count of zone threadIdx.x (threads < Z)
     for (int c0 = 0; c0 < n_steps; c0 += flush) {
         const int c1 = min(n_steps, c0 + flush);
         for (int s = c0; s < c1; ++s) {
@@ -719,7 +726,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
 
             // the brick-wall rule's active bonds alternate: its candidates change
             // every step even when the occupancy does not
-            if (dirty || a.rule != 0) {
+            const bool rebuilt = dirty || a.rule != 0;
+            if (rebuilt) {
                 // ---- 1. zone counts: segmented scan of popcounts
                 int cnt = 0;
 #pragma unroll
@@ -924,13 +932,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 __syncwarp();
             }
 
-            // ---- zone counts of the step-start occupancy into the trace
+            // ---- zone counts of the step-start occupancy into the trace, as
+            //      changes: they can only change when the occupancy was rebuilt,
+            //      and the flush sums them over the steps of the chunk
             if constexpr (!GRAD) {
-                for (int pi = lane; pi < G * Z; pi += 32) {
-                    const int g2 = pi / Z;
-                    const int z = pi - g2 * Z;
-                    const int nz = S.Pb()[g2 * (Z + 1) + z + 1] - S.Pb()[g2 * (Z + 1) + z];
-                    if (nz != 0) atomicAdd(&tr[1 + z], nz);
+                if (rebuilt) {
+                    for (int pi = lane; pi < G * Z; pi += 32) {
+                        const int g2 = pi / Z;
+                        const int z = pi - g2 * Z;
+                        const int nz = S.Pb()[g2 * (Z + 1) + z + 1] - S.Pb()[g2 * (Z + 1) + z];
+                        const int dz = nz - S.Np()[pi];
+                        if (dz != 0) {
+                            atomicAdd(&tr[1 + z], dz);
+                            S.Np()[pi] = nz;
+                        }
+                    }
                 }
             }
             if (lane == 0) {
@@ -1170,17 +1186,20 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         // ---- flush this chunk's traces and counters
         if constexpr (GRAD) continue;
         __syncthreads();
-        const int nval = (c1 - c0) * (1 + Z);
-        for (int i = threadIdx.x; i < nval; i += blockDim.x) {
-            const int v = trace[i];
-            if (v != 0) {
-                const int64_t step = t0 + c0 + i / (1 + Z);
-                const int q = i % (1 + Z);
-                const unsigned long long add = (unsigned long long)(long long)v;
-                if (q == 0) atomicAdd(&a.J[step], add);
-                else atomicAdd(&a.Zc[step * Z + (q - 1)], add);
+        for (int i = threadIdx.x; i < c1 - c0; i += blockDim.x) {
+            const int v = trace[i * (1 + Z)];
+            if (v != 0) atomicAdd(&a.J[t0 + c0 + i], (unsigned long long)(long long)v);
+            trace[i * (1 + Z)] = 0;
+        }
+        if ((int)threadIdx.x < Z) {
+            // thread z carries the CTA's count of zone z from chunk to chunk
+            const int z = threadIdx.x;
+            for (int i = 0; i < c1 - c0; ++i) {
+                zrun += trace[i * (1 + Z) + 1 + z];
+                trace[i * (1 + Z) + 1 + z] = 0;
+                if (zrun != 0)
+                    atomicAdd(&a.Zc[(t0 + c0 + i) * Z + z], (unsigned long long)(long long)zrun);
             }
-            trace[i] = 0;
         }
         const unsigned m = __reduce_add_sync(FULL, n_move);
         if (lane == 0) {
