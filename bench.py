@@ -200,6 +200,7 @@ def run_reference(args):
 def run_kmc(args):
     import torch
     from paper_2511_09413_gb300 import kmc
+    from paper_2511_09413_gb300 import multigpu as MG
 
     rank, local_rank, world = _env_rank()
     torch.cuda.set_device(local_rank)
@@ -212,7 +213,7 @@ def run_kmc(args):
     n_needed = (args.warmup + args.steps) * args.chunk + 2 * args.chunk
     wl = W.hysteresis_65536x1024(R=args.rails, steps_per_cycle=100000, cycles=2)
     wl.V = _voltage(n_needed)
-    wl.device.instance = rank
+    wl.device.instance = MG.shard_instances(world, rank, world)[0]   # one instance per rank
     sim = kmc.Sim.from_workload(wl, stream=stream.cuda_stream)
     R, L = wl.device.R, wl.device.L
     su_per_step = R * L * args.chunk
@@ -227,8 +228,7 @@ def run_kmc(args):
           for _ in range(args.steps)]
     clocks = ClockSampler(local_rank)
     clocks.start()
-    if dist:
-        dist.barrier()
+    MG.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(args.steps):
@@ -237,18 +237,14 @@ def run_kmc(args):
         sim.step_n(args.chunk)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    MG.barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms = sum(ms_steps)
     cnt1 = sim.counters()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * su_per_step * args.steps / (ms / 1e3)
+    ms = MG.max_over_ranks(ms, device="cuda")
+    value = MG.whole_job_rate([su_per_step * args.steps] * world, ms / 1e3)
 
     # end to end through the C ABI with host buffers: voltage chunk in, traces out
     from paper_2511_09413_gb300.kmc import kmc_observables, kmc_set_voltage
@@ -256,8 +252,7 @@ def run_kmc(args):
     Jpin = torch.empty(args.chunk, dtype=torch.int64, pin_memory=True).numpy()
     Zpin = torch.empty((args.chunk, wl.device.Z), dtype=torch.int64, pin_memory=True).numpy()
     e2e_steps = max(1, min(args.steps, 5))
-    if dist:
-        dist.barrier()
+    MG.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -267,12 +262,8 @@ def run_kmc(args):
         sim.step_n(args.chunk)
         kmc_observables(sim.h, first, args.chunk, Jpin, Zpin, None)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * su_per_step * e2e_steps / e2e_s
+    e2e_s = MG.max_over_ranks(time.perf_counter() - t0, device="cuda")
+    e2e_value = MG.whole_job_rate([su_per_step * e2e_steps] * world, e2e_s)
 
     if rank == 0:
         hbm, hbm_src, sm_max = _peaks()
