@@ -354,7 +354,7 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
                                             float fhi, bool exact, uint32_t xy, uint32_t xw)
 {
     const uint16_t dsc = S.list()[i];
-    const int site = dsc & 0x7FF, g2 = dsc >> 11;
+    const int site = dsc & 0x7FF, g2 = LPR == 32 ? 0 : dsc >> 11;
     const uint32_t r2 = (uint32_t)(rail0 + g2);
     // the bounded decision needs only the high words (x1, x3) of the draw; the
     // exact pass recomputes the whole block
@@ -826,7 +826,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     uint32_t m = cand[j];
                     const uint32_t base = (uint32_t)(32 * (wbase + j)) | ((uint32_t)seg << 11);
                     while (m) {
-                        S.list()[pos++] = (uint16_t)(base + (uint32_t)(__ffs(m) - 1));
+                        const uint32_t site = base + (uint32_t)(__ffs(m) - 1);
+                        // with one rail per warp the rail-slot bits carry the zone
+                        S.list()[pos++] = (uint16_t)(G == 1 ? site | ((uint32_t)zone_tab[site] << 11)
+                                                            : site);
                         m &= m - 1;
                     }
                 }
@@ -972,7 +975,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
                         const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
                                                rk0, rk1);
-                        const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
+                        const int ts = i >= n_inner ? G * Z + (i - n_inner)
+                                                    : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]);
                         th[q] = S.rm4()[ts];
                         xy[q] = x.y;
                         xw[q] = x.w;
@@ -1033,7 +1037,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
                                                rk0, rk1);
                         // electrode sites have their own entries after the G Z zone entries
-                        const int ts = i >= n_inner ? G * Z + (i - n_inner) : g * Z + zone_tab[site];
+                        const int ts = i >= n_inner ? G * Z + (i - n_inner)
+                                                    : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]);
                         const uint2 rm = S.rm()[ts];
                         xy[q] = x.y;
                         xw[q] = x.w;
