@@ -272,6 +272,8 @@ def run_kmc(args):
         sm_mhz = clk.get("sm_mhz") or sm_max
         alu_peak = SMS * IMAD_PER_SM_PER_CLK * sm_max * 1e6 / PHILOX_IMAD / 1e9   # G blocks/s
         achieved = draws / per_launch_s / 1e9
+        from paper_2511_09413_gb300.kmc import kmc_philox_probe
+        probe = kmc_philox_probe(stream.cuda_stream) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -288,6 +290,9 @@ def run_kmc(args):
                          "traffic_unit": "DRAM bytes per launch (ncu, scaled by rails)",
                          "peak_basis": "%d SMs x %d IMAD lanes/clk x %.0f MHz / %d IMAD ops per block" % (
                              SMS, IMAD_PER_SM_PER_CLK, sm_max, PHILOX_IMAD),
+                         "philox_only_probe": {"achieved": probe, "frac": achieved / probe,
+                                               "basis": "kmc_philox_probe: the draw loop's Philox "
+                                                        "blocks alone, measured in this run"},
                          "hbm_basis": {"achieved_GBps": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9,
                                        "peak_GBps": hbm, "peak_source": hbm_src,
                                        "frac": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9 / hbm,

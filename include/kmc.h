@@ -185,6 +185,12 @@ int kmc_accept_path(const kmc_handle *h);
 int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, double grad_out[4],
              double stderr_out[4]);
 
+/* Measurement aid: the GPU's throughput of Philox4x32-10 blocks as the sweep
+ * draws them (same routine, the two words the draw loop consumes), with no
+ * other work, in blocks per second; the integer-pipe ceiling of kmc_step_n.
+ * Runs about 50 ms on cuda_stream (allocates a small buffer; synchronizes). */
+int kmc_philox_probe(void *cuda_stream, double *blocks_per_s);
+
 /* Current absolute step of the handle. */
 int64_t kmc_current_step(const kmc_handle *h);
 

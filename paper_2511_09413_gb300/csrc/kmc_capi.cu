@@ -458,6 +458,35 @@ int kmc_near_threshold_log(kmc_handle *h, kmc_log_entry *out, int64_t cap, int64
     return KMC_OK;
 }
 
+int kmc_philox_probe(void *cuda_stream, double *blocks_per_s)
+{
+    if (!blocks_per_s) return fail(KMC_E_ARG, "blocks_per_s is NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int grid = sms * 8, iters = 20000;   // 8 CTAs of 256 threads per SM
+    uint32_t *sink = nullptr;
+    CK(cudaMallocAsync((void **)&sink, sizeof(uint32_t) * (size_t)grid * 256, s), "probe buffer");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = philox_probe(grid, iters / 10, sink, s);      // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = philox_probe(grid, iters, sink, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(sink, s);
+    cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "Philox probe");
+    *blocks_per_s = (double)grid * 256.0 * 4.0 * (double)iters / ((double)ms * 1e-3);
+    return KMC_OK;
+}
+
 int kmc_counters(kmc_handle *h, uint64_t out[3])
 {
     if (!h || !out) return fail(KMC_E_ARG, "handle or out is NULL");

@@ -1400,6 +1400,31 @@ cudaError_t smem_attr()
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
+// Philox-only throughput probe: the draw loop's Philox4x32-10 blocks and
+// nothing else (counter (i, thread, 0, 0), the two high words consumed as in
+// the draw loop), four independent blocks per iteration.  Measures the
+// integer-pipe ceiling that the sweep's roofline refers to.
+__global__ void __launch_bounds__(256) philox_probe_kernel(int iters, uint32_t k0, uint32_t k1,
+                                                           uint32_t *sink)
+{
+    uint32_t rk0[10], rk1[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        rk0[i] = k0 + 0x9E3779B9u * (uint32_t)i;
+        rk1[i] = k1 + 0xBB67AE85u * (uint32_t)i;
+    }
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 x = philox((uint32_t)(4 * it + q), tid, 0u, 0u, rk0, rk1);
+            acc ^= x.y + x.w;
+        }
+    }
+    if (acc == 0x12345678u) sink[tid] = acc;   // keeps the work; practically never stores
+}
+
 }  // namespace
 
 size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite, bool acc)
@@ -1439,6 +1464,12 @@ cudaError_t grad_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s
     case 16: return grad_launch_t<16, 1>(a, l, s);
     default: return grad_launch_t<32, 1>(a, l, s);
     }
+}
+
+cudaError_t philox_probe(int grid, int iters, uint32_t *sink, cudaStream_t s)
+{
+    philox_probe_kernel<<<grid, 256, 0, s>>>(iters, 0x243F6A88u, 0x85A308D3u, sink);
+    return cudaGetLastError();
 }
 
 cudaError_t grad_reduce(const double *gstate, int64_t R, const int32_t *N0, int L, double fill,

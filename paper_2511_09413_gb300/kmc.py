@@ -73,7 +73,7 @@ EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "
            "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
            "kmc_batch_current_step", "kmc_batch_destroy", "kmc_set_accept_path",
            "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path", "kmc_grad",
-           "kmc_batch_grad"]
+           "kmc_batch_grad", "kmc_philox_probe"]
 
 _lib = None
 
@@ -119,6 +119,8 @@ def load(path: str = LIB_PATH):
     L.kmc_batch_destroy.restype = None
     L.kmc_grad.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                            P(ctypes.c_double)]
+    L.kmc_philox_probe.argtypes = [vp, P(ctypes.c_double)]
+    L.kmc_philox_probe.restype = ctypes.c_int
     L.kmc_batch_grad.argtypes = [vp, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double),
                                  P(ctypes.c_double), P(ctypes.c_double)]
     L.kmc_batch_grad.restype = ctypes.c_int
@@ -426,6 +428,13 @@ def kmc_batch_grad(b: int, inst: int, n: int, Z: int, dLoss_dJ: Optional[np.ndar
                                  _ptr(wZ, ctypes.c_double), _ptr(g, ctypes.c_double),
                                  _ptr(se, ctypes.c_double)))
     return g, se
+
+
+def kmc_philox_probe(stream: Optional[int] = None) -> float:
+    """Philox4x32-10 blocks per second with no other work (kmc_philox_probe)."""
+    out = ctypes.c_double()
+    _check(load().kmc_philox_probe(ctypes.c_void_p(stream or 0), ctypes.byref(out)))
+    return out.value
 
 
 def kmc_batch_current_step(b: int) -> int:

@@ -262,3 +262,10 @@ def test_brick_wall_rule_rejected_by_gradient_pass(kmc):
     with pytest.raises(kmc.KmcError):
         sim.grad(np.ones(10), None)
     sim.close()
+
+
+def test_philox_probe_reports_a_rate(kmc):
+    """The Philox-only probe runs and reports a rate between the sweep's own
+    draw rate and the IMAD-issue bound (152 SMs x 64 lanes x 2.07 GHz / 40)."""
+    r = kmc.kmc_philox_probe()
+    assert 1e11 < r < 8e11, r
