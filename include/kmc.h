@@ -242,6 +242,13 @@ int kmc_batch_accept_path(const kmc_batch *b);
  * occupancy).  Synchronizes the batch's stream. */
 int kmc_batch_grad(kmc_batch *b, int32_t inst, const double *dLoss_dJ, const double *dLoss_dZc,
                    double grad_out[4], double stderr_out[4]);
+/* The gradient passes of every device of the batch in one persistent launch
+ * (the devices' rail tiles as work items, as the forward batch).  For device
+ * i, dLoss_dJ[i] and dLoss_dZc[i] are as kmc_grad's (either array of pointers,
+ * or an entry, may be NULL); grad_out[i][4] and stderr_out[i][4] (may be NULL)
+ * receive what kmc_grad would return for that device alone.  Synchronizes. */
+int kmc_batch_grad_all(kmc_batch *b, const double *const *dLoss_dJ, const double *const *dLoss_dZc,
+                       double *grad_out, double *stderr_out);
 int64_t kmc_batch_current_step(const kmc_batch *b);
 void kmc_batch_destroy(kmc_batch *b);
 

@@ -427,6 +427,109 @@ int kmc_batch_grad(kmc_batch *b, int32_t inst, const double *dLoss_dJ, const dou
     return kmc_grad(b->dev[inst], dLoss_dJ, dLoss_dZc, grad_out, stderr_out);
 }
 
+int kmc_batch_grad_all(kmc_batch *b, const double *const *dLoss_dJ, const double *const *dLoss_dZc,
+                       double *grad_out, double *stderr_out)
+{
+    if (!b || !grad_out) return fail(KMC_E_ARG, "batch or grad_out is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    const int n_inst = (int)b->dev.size();
+    std::vector<double> out((size_t)n_inst * 8, 0.0);
+    std::vector<SweepArgs> gargs((size_t)n_inst);
+    std::vector<char> active((size_t)n_inst, 0);
+    int dev = 0, max_smem = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (max_smem <= 0) max_smem = 48 * 1024;
+    max_smem = std::min(max_smem, 200 * 1024);
+    int n_active = 0;
+    for (int i = 0; i < n_inst && b->t > 0; ++i) {
+        const double *wJ = dLoss_dJ ? dLoss_dJ[i] : nullptr;
+        const double *wZ = dLoss_dZc ? dLoss_dZc[i] : nullptr;
+        if (!wJ && !wZ) continue;
+        int rc = grad_prepare(b->dev[i], wJ, wZ, &gargs[(size_t)i]);
+        if (rc) return rc;
+        active[(size_t)i] = 1;
+        ++n_active;
+    }
+    if (n_active > 0) {
+        // CTA size: 8 warps unless some device's tile needs less shared memory
+        int warps = 8;
+        auto smem_for = [&](int w) {
+            size_t m = 0;
+            for (int i = 0; i < n_inst; ++i)
+                if (active[(size_t)i]) {
+                    const kmc_params &p = b->dev[(size_t)i]->p;
+                    int wpl = 1;
+                    const int lpr = sweep_pick_lpr(p.n_sites, &wpl);
+                    m = std::max(m, grad_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, w));
+                }
+            return m;
+        };
+        while (warps > 1 && smem_for(warps) > (size_t)max_smem) warps >>= 1;
+        const size_t smem = smem_for(warps);
+        if (smem > (size_t)max_smem)
+            return fail(KMC_E_ARG, "batched gradient pass: shared memory exceeds the device limit");
+        // work items, longest tiles first
+        std::vector<BatchItem> items;
+        std::vector<int64_t> cost;
+        for (int i = 0; i < n_inst; ++i) {
+            if (!active[(size_t)i]) continue;
+            const kmc_params &p = b->dev[(size_t)i]->p;
+            int wpl = 1;
+            const int lpr = sweep_pick_lpr(p.n_sites, &wpl);
+            const int64_t tile = (int64_t)(32 / lpr) * warps;
+            for (int64_t r0 = 0; r0 < p.n_rails; r0 += tile) {
+                BatchItem it;
+                it.inst = i;
+                it.kind = sweep_kind(lpr, wpl);
+                it.tile_rail0 = r0;
+                items.push_back(it);
+                cost.push_back(std::min<int64_t>(tile, p.n_rails - r0) * p.n_sites);
+            }
+        }
+        std::vector<size_t> order(items.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::vector<BatchItem> sorted(items.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        SweepArgs *ginst = nullptr;
+        BatchItem *gitems = nullptr;
+        BCK(cudaMallocAsync((void **)&ginst, sizeof(SweepArgs) * (size_t)n_inst, b->user), "grad args");
+        e = cudaMallocAsync((void **)&gitems, sizeof(BatchItem) * sorted.size(), b->user);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ginst, b->user);
+            return cuda_fail(e, "grad items");
+        }
+        BatchArgs a = batch_args(b, (int)b->t);
+        a.inst = ginst;
+        a.items = gitems;
+        a.n_items = (int)sorted.size();
+        const int grid = std::max(1, std::min(a.n_items, sms * 2 * std::max(1, 8 / warps)));
+        if ((e = cudaMemcpyAsync(ginst, gargs.data(), sizeof(SweepArgs) * (size_t)n_inst,
+                                 cudaMemcpyHostToDevice, b->user)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(gitems, sorted.data(), sizeof(BatchItem) * sorted.size(),
+                                 cudaMemcpyHostToDevice, b->user)) == cudaSuccess &&
+            (e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned), b->user)) == cudaSuccess &&
+            (e = batch_grad_launch(a, grid, warps, smem, b->user)) == cudaSuccess)
+            e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned), b->user);   // re-arm for the forward
+        cudaFreeAsync(gitems, b->user);
+        cudaFreeAsync(ginst, b->user);
+        if (e != cudaSuccess) return cuda_fail(e, "batched gradient pass");
+        for (int i = 0; i < n_inst; ++i)
+            if (active[(size_t)i]) {
+                int rc = grad_reduce_out(b->dev[(size_t)i], &out[(size_t)i * 8]);
+                if (rc) return rc;
+            }
+        BCK(cudaStreamSynchronize(b->user), "batched gradient pass");
+    }
+    for (int i = 0; i < n_inst; ++i)
+        grad_outputs(b->dev[(size_t)i], &out[(size_t)i * 8], grad_out + 4 * (size_t)i,
+                     stderr_out ? stderr_out + 4 * (size_t)i : nullptr);
+    return KMC_OK;
+}
+
 int64_t kmc_batch_current_step(const kmc_batch *b) { return b ? b->t : -1; }
 
 void kmc_batch_destroy(kmc_batch *b)

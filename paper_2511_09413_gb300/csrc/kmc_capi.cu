@@ -345,6 +345,154 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
 
 }  // namespace
 
+// Gradient pass, host side (shared by kmc_grad and kmc_batch_grad_all):
+// validate, allocate the pass's buffers at the first call, upload the
+// observable's per-step coefficients (with the forward's totals for the
+// leave-one-out baselines), copy the step-0 checkpoint to the replay
+// buffer, clear the per-rail state, and fill the replay's arguments.
+int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, SweepArgs *gout)
+{
+    if (h->P0site)
+        return fail(KMC_E_ARG, "kmc_grad needs a scalar barrier (the handle has per-site Ea)");
+    if (h->p.update_rule != 0)
+        return fail(KMC_E_ARG, "kmc_grad follows the synchronous update (update_rule 0)");
+    const kmc_params &p = h->p;
+    const int64_t R = p.n_rails, L = p.n_sites, Z = p.n_zones, n = h->t;
+    if (n > ((int64_t)1 << 30)) return fail(KMC_E_RANGE, "gradient pass over more than 2^30 steps");
+    cudaStream_t s = h->stream;
+    const size_t occ_bytes = (size_t)(R * h->stride);
+    const size_t nt = (size_t)std::max<int64_t>(h->n_total, 1);
+    if (!h->g_occ) {
+        h->g_occ = (uint8_t *)h->alloc(occ_bytes);
+        h->g_state = (double *)h->alloc(sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1));
+        h->g_wJ = (double *)h->alloc(sizeof(double) * nt);
+        h->g_fJab = (double *)h->alloc(sizeof(double) * 2 * nt);
+        h->g_fZa = (double *)h->alloc(sizeof(double) * nt * (size_t)Z);
+        h->g_fZb = (double *)h->alloc(sizeof(double) * nt);
+        h->g_out = (double *)h->alloc(sizeof(double) * 8);
+        h->g_misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
+        h->g_args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
+        if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_fJab || !h->g_fZa || !h->g_fZb ||
+            !h->g_out || !h->g_misc || !h->g_args_dev)
+            return fail(KMC_E_NOMEM, "device allocation failed (gradient pass)");
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (dLoss_dJ && !isfinite(dLoss_dJ[i]))
+            return fail(KMC_E_ARG, "dLoss_dJ[%lld] is not finite", (long long)i);
+    if (dLoss_dZc)
+        for (int64_t i = 0; i < n * Z; ++i)
+            if (!isfinite(dLoss_dZc[i]))
+                return fail(KMC_E_ARG, "dLoss_dZc[%lld] is not finite", (long long)i);
+    // the forward's totals give each step's leave-one-out baseline:
+    //   fJ = wJ (J_r - (J_t - J_r) / (R - 1)) = aJ J_r - bJ, and likewise fZ
+    std::vector<int64_t> Jt((size_t)n), Zt;
+    CK(cudaMemcpyAsync(Jt.data(), h->J, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s),
+       "copy J");
+    if (dLoss_dZc) {
+        Zt.resize((size_t)(n * Z));
+        CK(cudaMemcpyAsync(Zt.data(), h->Zc, sizeof(int64_t) * (size_t)(n * Z),
+                           cudaMemcpyDeviceToHost, s),
+           "copy Zc");
+    }
+    CK(cudaStreamSynchronize(s), "totals");
+    const double loo = R > 1 ? (double)(R - 1) : 0.0;
+    const double scale = R > 1 ? (double)R / loo : 1.0;
+    std::vector<double> fJab, fZa, fZb;
+    if (dLoss_dJ) {
+        fJab.resize((size_t)(2 * n));
+        for (int64_t i = 0; i < n; ++i) {
+            fJab[2 * i] = dLoss_dJ[i] * scale;
+            fJab[2 * i + 1] = loo > 0.0 ? dLoss_dJ[i] * ((double)Jt[i] / loo) : 0.0;
+        }
+        CK(cudaMemcpyAsync(h->g_wJ, dLoss_dJ, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s),
+           "copy dLoss_dJ");
+        CK(cudaMemcpyAsync(h->g_fJab, fJab.data(), sizeof(double) * (size_t)(2 * n),
+                           cudaMemcpyHostToDevice, s),
+           "copy fJ coefficients");
+    }
+    if (dLoss_dZc) {
+        fZa.resize((size_t)(n * Z));
+        fZb.assign((size_t)n, 0.0);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t z = 0; z < Z; ++z) {
+                const double w = dLoss_dZc[i * Z + z];
+                fZa[(size_t)(i * Z + z)] = w * scale;
+                if (loo > 0.0) fZb[(size_t)i] += w * ((double)Zt[(size_t)(i * Z + z)] / loo);
+            }
+        CK(cudaMemcpyAsync(h->g_fZa, fZa.data(), sizeof(double) * (size_t)(n * Z),
+                           cudaMemcpyHostToDevice, s),
+           "copy fZ coefficients");
+        CK(cudaMemcpyAsync(h->g_fZb, fZb.data(), sizeof(double) * (size_t)n,
+                           cudaMemcpyHostToDevice, s),
+           "copy fZ offsets");
+    }
+    CK(cudaMemcpyAsync(h->g_occ, h->occ_init, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
+    CK(cudaMemsetAsync(h->g_state, 0, sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1), s),
+       "memset");
+    CK(cudaMemsetAsync(h->g_misc, 0, sizeof(unsigned long long) * 8, s), "memset");
+    // the replay: same trajectory (same counters), no traces, no log
+    SweepArgs ga = h->args;
+    ga.occ = h->g_occ;
+    ga.self = h->g_args_dev;
+    ga.J = nullptr;
+    ga.Zc = nullptr;
+    ga.log = h->log;
+    ga.log_cap = 0;
+    ga.log_count = h->g_misc;
+    ga.counters = h->g_misc + 1;
+    ga.wJ = dLoss_dJ ? h->g_wJ : nullptr;
+    ga.fJab = dLoss_dJ ? (const double2 *)h->g_fJab : nullptr;
+    ga.fZa = dLoss_dZc ? h->g_fZa : nullptr;
+    ga.fZb = dLoss_dZc ? h->g_fZb : nullptr;
+    ga.gstate = h->g_state;
+    ga.alpha = p.alpha_V;
+    const double kT = 8.6173e-5 * p.T_K;
+    ga.tdev_kT = ((double)L * p.site_spacing_nm) * kT;
+    CK(cudaMemcpyAsync(h->g_args_dev, &ga, sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
+       "copy args");
+    ga.t0 = 0;
+    ga.n_steps = (int32_t)n;
+    ga.flush = (int32_t)n;
+    *gout = ga;
+    return KMC_OK;
+}
+
+// Per-rail sums and standard errors into out[8] (enqueued on the handle's stream).
+int kmc::grad_reduce_out(kmc_handle *h, double *out_host)
+{
+    const kmc_params &p = h->p;
+    const bool has_rho = p.init_mode == 1 && p.fill > 0.0 && p.fill < 1.0;
+    const double kT = 8.6173e-5 * p.T_K;
+    // d ln P0 / d Ea and d ln P0 / d nu (Eq. 1, P0 = 1 - exp(-x), x = 2 Gamma0 dt)
+    const double x = 2.0 * (p.nu_Hz * exp(-p.Ea_eV / kT)) * p.dt_s;
+    const double P0 = -expm1(-x);
+    const double cEa = -((x / kT) * exp(-x)) / P0;
+    const double cnu = ((x / p.nu_Hz) * exp(-x)) / P0;
+    CK(grad_reduce(h->g_state, p.n_rails, h->N0, p.n_sites, p.fill, has_rho ? 1 : 0, cEa, cnu,
+                   h->g_out, h->stream),
+       "gradient reduce launch");
+    CK(cudaMemcpyAsync(out_host, h->g_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream),
+       "copy gradient");
+    return KMC_OK;
+}
+
+// grad_out / stderr_out from the reduced sums; the fill entry is NaN unless
+// the placement was Bernoulli(fill).
+void kmc::grad_outputs(const kmc_handle *h, const double out[8], double grad_out[4],
+                       double stderr_out[4])
+{
+    const kmc_params &p = h->p;
+    const bool has_rho = p.init_mode == 1 && p.fill > 0.0 && p.fill < 1.0;
+    for (int i = 0; i < 4; ++i) {
+        grad_out[i] = out[i];
+        if (stderr_out) stderr_out[i] = out[4 + i];
+    }
+    if (!has_rho) {
+        grad_out[3] = NAN;
+        if (stderr_out) stderr_out[3] = NAN;
+    }
+}
+
 extern "C" {
 
 int kmc_set_allocator(kmc_alloc_fn alloc, kmc_free_fn free_fn, void *ctx)
@@ -519,100 +667,12 @@ int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, dou
         return fail(KMC_E_ARG, "kmc_grad follows the synchronous update (update_rule 0)");
     const kmc_params &p = h->p;
     const int64_t R = p.n_rails, L = p.n_sites, Z = p.n_zones, n = h->t;
-    const bool has_rho = p.init_mode == 1 && p.fill > 0.0 && p.fill < 1.0;
     double out[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     cudaStream_t s = h->stream;
     if (n > 0 && (dLoss_dJ || dLoss_dZc)) {
-        const size_t occ_bytes = (size_t)(R * h->stride);
-        const size_t nt = (size_t)std::max<int64_t>(h->n_total, 1);
-        if (!h->g_occ) {
-            h->g_occ = (uint8_t *)h->alloc(occ_bytes);
-            h->g_state = (double *)h->alloc(sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1));
-            h->g_wJ = (double *)h->alloc(sizeof(double) * nt);
-            h->g_fJab = (double *)h->alloc(sizeof(double) * 2 * nt);
-            h->g_fZa = (double *)h->alloc(sizeof(double) * nt * (size_t)Z);
-            h->g_fZb = (double *)h->alloc(sizeof(double) * nt);
-            h->g_out = (double *)h->alloc(sizeof(double) * 8);
-            h->g_misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
-            h->g_args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
-            if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_fJab || !h->g_fZa || !h->g_fZb ||
-                !h->g_out || !h->g_misc || !h->g_args_dev)
-                return fail(KMC_E_NOMEM, "device allocation failed (gradient pass)");
-        }
-        for (int64_t i = 0; i < n; ++i)
-            if (dLoss_dJ && !isfinite(dLoss_dJ[i]))
-                return fail(KMC_E_ARG, "dLoss_dJ[%lld] is not finite", (long long)i);
-        if (dLoss_dZc)
-            for (int64_t i = 0; i < n * Z; ++i)
-                if (!isfinite(dLoss_dZc[i]))
-                    return fail(KMC_E_ARG, "dLoss_dZc[%lld] is not finite", (long long)i);
-        // the forward's totals give each step's leave-one-out baseline:
-        //   fJ = wJ (J_r - (J_t - J_r) / (R - 1)) = aJ J_r - bJ, and likewise fZ
-        std::vector<int64_t> Jt((size_t)n), Zt;
-        CK(cudaMemcpyAsync(Jt.data(), h->J, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s),
-           "copy J");
-        if (dLoss_dZc) {
-            Zt.resize((size_t)(n * Z));
-            CK(cudaMemcpyAsync(Zt.data(), h->Zc, sizeof(int64_t) * (size_t)(n * Z),
-                               cudaMemcpyDeviceToHost, s),
-               "copy Zc");
-        }
-        CK(cudaStreamSynchronize(s), "totals");
-        const double loo = R > 1 ? (double)(R - 1) : 0.0;
-        const double scale = R > 1 ? (double)R / loo : 1.0;
-        std::vector<double> fJab, fZa, fZb;
-        if (dLoss_dJ) {
-            fJab.resize((size_t)(2 * n));
-            for (int64_t i = 0; i < n; ++i) {
-                fJab[2 * i] = dLoss_dJ[i] * scale;
-                fJab[2 * i + 1] = loo > 0.0 ? dLoss_dJ[i] * ((double)Jt[i] / loo) : 0.0;
-            }
-            CK(cudaMemcpyAsync(h->g_wJ, dLoss_dJ, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, s),
-               "copy dLoss_dJ");
-            CK(cudaMemcpyAsync(h->g_fJab, fJab.data(), sizeof(double) * (size_t)(2 * n),
-                               cudaMemcpyHostToDevice, s),
-               "copy fJ coefficients");
-        }
-        if (dLoss_dZc) {
-            fZa.resize((size_t)(n * Z));
-            fZb.assign((size_t)n, 0.0);
-            for (int64_t i = 0; i < n; ++i)
-                for (int64_t z = 0; z < Z; ++z) {
-                    const double w = dLoss_dZc[i * Z + z];
-                    fZa[(size_t)(i * Z + z)] = w * scale;
-                    if (loo > 0.0) fZb[(size_t)i] += w * ((double)Zt[(size_t)(i * Z + z)] / loo);
-                }
-            CK(cudaMemcpyAsync(h->g_fZa, fZa.data(), sizeof(double) * (size_t)(n * Z),
-                               cudaMemcpyHostToDevice, s),
-               "copy fZ coefficients");
-            CK(cudaMemcpyAsync(h->g_fZb, fZb.data(), sizeof(double) * (size_t)n,
-                               cudaMemcpyHostToDevice, s),
-               "copy fZ offsets");
-        }
-        CK(cudaMemcpyAsync(h->g_occ, h->occ_init, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
-        CK(cudaMemsetAsync(h->g_state, 0, sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1), s),
-           "memset");
-        CK(cudaMemsetAsync(h->g_misc, 0, sizeof(unsigned long long) * 8, s), "memset");
-        // the replay: same trajectory (same counters), no traces, no log
-        SweepArgs ga = h->args;
-        ga.occ = h->g_occ;
-        ga.self = h->g_args_dev;
-        ga.J = nullptr;
-        ga.Zc = nullptr;
-        ga.log = h->log;
-        ga.log_cap = 0;
-        ga.log_count = h->g_misc;
-        ga.counters = h->g_misc + 1;
-        ga.wJ = dLoss_dJ ? h->g_wJ : nullptr;
-        ga.fJab = dLoss_dJ ? (const double2 *)h->g_fJab : nullptr;
-        ga.fZa = dLoss_dZc ? h->g_fZa : nullptr;
-        ga.fZb = dLoss_dZc ? h->g_fZb : nullptr;
-        ga.gstate = h->g_state;
-        ga.alpha = p.alpha_V;
-        const double kT = 8.6173e-5 * p.T_K;
-        ga.tdev_kT = ((double)L * p.site_spacing_nm) * kT;
-        CK(cudaMemcpyAsync(h->g_args_dev, &ga, sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
-           "copy args");
+        SweepArgs ga;
+        int rc = grad_prepare(h, dLoss_dJ, dLoss_dZc, &ga);
+        if (rc) return rc;
         SweepLaunch l = h->launch;
         int dev = 0, max_smem = 0;
         cudaGetDevice(&dev);
@@ -628,30 +688,12 @@ int kmc_grad(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, dou
         l.smem = grad_smem_bytes(l.lpr, l.wpl, (int)Z, (int)L, warps);
         const int64_t rails_per_cta = (int64_t)(32 / l.lpr) * warps;
         l.grid = (int)((R + rails_per_cta - 1) / rails_per_cta);
-        for (int64_t t0 = 0; t0 < n; t0 += (int64_t)1 << 30) {
-            ga.t0 = t0;
-            ga.n_steps = (int32_t)std::min<int64_t>(n - t0, (int64_t)1 << 30);
-            ga.flush = ga.n_steps;
-            CK(grad_launch(ga, l, s), "gradient pass launch");
-        }
-        // d ln P0 / d Ea and d ln P0 / d nu (Eq. 1, P0 = 1 - exp(-x), x = 2 Gamma0 dt)
-        const double x = 2.0 * (p.nu_Hz * exp(-p.Ea_eV / kT)) * p.dt_s;
-        const double P0 = -expm1(-x);
-        const double cEa = -((x / kT) * exp(-x)) / P0;
-        const double cnu = ((x / p.nu_Hz) * exp(-x)) / P0;
-        CK(grad_reduce(h->g_state, R, h->N0, (int)L, p.fill, has_rho ? 1 : 0, cEa, cnu, h->g_out, s),
-           "gradient reduce launch");
-        CK(cudaMemcpyAsync(out, h->g_out, sizeof(out), cudaMemcpyDeviceToHost, s), "copy gradient");
+        CK(grad_launch(ga, l, s), "gradient pass launch");
+        rc = grad_reduce_out(h, out);
+        if (rc) return rc;
         CK(cudaStreamSynchronize(s), "gradient pass");
     }
-    for (int i = 0; i < 4; ++i) {
-        grad_out[i] = out[i];
-        if (stderr_out) stderr_out[i] = out[4 + i];
-    }
-    if (!has_rho) {
-        grad_out[3] = NAN;
-        if (stderr_out) stderr_out[3] = NAN;
-    }
+    grad_outputs(h, out, grad_out, stderr_out);
     return KMC_OK;
 }
 

@@ -84,3 +84,10 @@ struct kmc_handle {
         cudaStreamSynchronize(stream);
     }
 };
+
+namespace kmc {
+// Host side of the gradient pass (kmc_capi.cu), shared with the batch runtime.
+int grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss_dZc, SweepArgs *ga);
+int grad_reduce_out(kmc_handle *h, double *out_host);
+void grad_outputs(const kmc_handle *h, const double out[8], double grad_out[4], double stderr_out[4]);
+}  // namespace kmc

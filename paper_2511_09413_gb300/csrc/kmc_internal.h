@@ -125,6 +125,9 @@ size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bo
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
+// gradient passes of a batch: one persistent launch over (device, tile) items
+// whose per-device arguments (b.inst) are gradient-pass arguments
+cudaError_t batch_grad_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s);
 // Philox-only probe: grid CTAs of 256 threads, each thread 4 x iters blocks
 cudaError_t philox_probe(int grid, int iters, uint32_t *sink, cudaStream_t s);
 // gradient pass: shared memory of a launch, the launch, and the final sum

@@ -1363,6 +1363,38 @@ __global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs b)
     }
 }
 
+// Gradient passes of a batch of devices in one persistent launch: CTAs take
+// (device, rail tile) items and replay that device's steps 0 .. n_steps-1
+// with its gradient-pass arguments (the same tile body as sweep_grad_kernel).
+__global__ void __launch_bounds__(256, 2) sweep_batch_grad_kernel(const BatchArgs b)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ SweepArgs ia;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.work, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.n_items) break;
+        const BatchItem it = b.items[item];
+        const uint32_t *src = (const uint32_t *)&b.inst[it.inst];
+        for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs) / 4); i += blockDim.x)
+            ((uint32_t *)&ia)[i] = src[i];
+        __syncthreads();
+        const int n = ia.n_steps;
+        switch (it.kind) {
+        case 0: sweep_tile<1, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        case 1: sweep_tile<2, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        case 2: sweep_tile<4, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        case 3: sweep_tile<8, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        case 4: sweep_tile<16, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        case 5: sweep_tile<32, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        default: sweep_tile<32, 2, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
+        }
+        __syncthreads();
+    }
+}
+
 // Advance the batch's step counter and re-arm its work counter.
 __global__ void batch_advance_kernel(int64_t *t0, unsigned *work, int n_steps)
 {
@@ -1464,6 +1496,19 @@ cudaError_t grad_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s
     case 16: return grad_launch_t<16, 1>(a, l, s);
     default: return grad_launch_t<32, 1>(a, l, s);
     }
+}
+
+cudaError_t batch_grad_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_batch_grad_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    sweep_batch_grad_kernel<<<grid, warps * 32, smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t philox_probe(int grid, int iters, uint32_t *sink, cudaStream_t s)

@@ -10,8 +10,9 @@ persistent launch at the current (Ea, kappa), and the loss
     loss = sum over devices d, samples k of (G_d(t_k) - G*_d(t_k))^2
 
 has the gradient sum_{d,k} 2 (G_d(t_k) - G*_d(t_k)) dE[G_d(t_k)]/d theta, whose
-expectations come from the backward pass of each device (kmc_batch_grad) with
-the weights 2 (G - G*) / N on the zone-0 counts.  The sampled G replaces its
+expectations come from the devices' backward passes, run together in one
+batched launch (kmc_batch_grad_all), with the weights 2 (G - G*) / N on the
+zone-0 counts.  The sampled G replaces its
 expectation in the factor 2 (G - G*), which is exact as the devices' rail
 counts grow (G's own variance is O(1 / ions)).
 """
@@ -73,14 +74,15 @@ class MaterialFit:
                 G[i] = Zc[self.sample_steps, 0] / N[i]
             r = G - self.target
             loss = float((r ** 2).sum())
-            grad = np.zeros(2)
-            var = np.zeros(2)
+            wZs = []
             for i in range(n):
                 wZ = np.zeros((self.n_steps, devs[i].Z))
                 wZ[self.sample_steps, 0] = 2.0 * r[i] / N[i]
-                g, se = b.grad(i, None, wZ)
-                grad += g[[0, 2]]
-                var += se[[0, 2]] ** 2
+                wZs.append(wZ)
+            # every device's backward pass in one batched launch
+            g, se = b.grad_all(None, wZs)
+            grad = g[:, [0, 2]].sum(axis=0)
+            var = (se[:, [0, 2]] ** 2).sum(axis=0)
             t2 = time.perf_counter()
         finally:
             b.close()

@@ -73,7 +73,7 @@ EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "
            "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
            "kmc_batch_current_step", "kmc_batch_destroy", "kmc_set_accept_path",
            "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path", "kmc_grad",
-           "kmc_batch_grad", "kmc_philox_probe"]
+           "kmc_batch_grad", "kmc_philox_probe", "kmc_batch_grad_all"]
 
 _lib = None
 
@@ -119,6 +119,9 @@ def load(path: str = LIB_PATH):
     L.kmc_batch_destroy.restype = None
     L.kmc_grad.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                            P(ctypes.c_double)]
+    L.kmc_batch_grad_all.argtypes = [vp, P(P(ctypes.c_double)), P(P(ctypes.c_double)),
+                                     P(ctypes.c_double), P(ctypes.c_double)]
+    L.kmc_batch_grad_all.restype = ctypes.c_int
     L.kmc_philox_probe.argtypes = [vp, P(ctypes.c_double)]
     L.kmc_philox_probe.restype = ctypes.c_int
     L.kmc_batch_grad.argtypes = [vp, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double),
@@ -430,6 +433,35 @@ def kmc_batch_grad(b: int, inst: int, n: int, Z: int, dLoss_dJ: Optional[np.ndar
     return g, se
 
 
+def kmc_batch_grad_all(b: int, shapes, n: int, dLoss_dJ=None, dLoss_dZc=None):
+    """(grad [n_inst, 4], stderr [n_inst, 4]) of every device in one launch;
+    dLoss_dJ / dLoss_dZc are sequences (entries may be None) or None."""
+    k = len(shapes)
+    keep = []
+
+    def table(ws, shape_of):
+        if ws is None:
+            return None
+        arr = (ctypes.POINTER(ctypes.c_double) * k)()
+        for i, w in enumerate(ws):
+            if w is None:
+                continue
+            a = np.ascontiguousarray(w, dtype=np.float64)
+            if a.shape != shape_of(i):
+                raise ValueError("weights of device %d must have shape %s" % (i, shape_of(i)))
+            keep.append(a)
+            arr[i] = _ptr(a, ctypes.c_double)
+        return arr
+
+    tJ = table(dLoss_dJ, lambda i: (n,))
+    tZ = table(dLoss_dZc, lambda i: (n, shapes[i][2]))
+    g = np.zeros((k, 4))
+    se = np.zeros((k, 4))
+    _check(load().kmc_batch_grad_all(ctypes.c_void_p(b), tJ, tZ, _ptr(g, ctypes.c_double),
+                                     _ptr(se, ctypes.c_double)))
+    return g, se
+
+
 def kmc_philox_probe(stream: Optional[int] = None) -> float:
     """Philox4x32-10 blocks per second with no other work (kmc_philox_probe)."""
     out = ctypes.c_double()
@@ -476,6 +508,10 @@ class Batch:
 
     def set_accept_path(self, mode: int = -1):
         kmc_batch_set_accept_path(self.h, mode)
+
+    def grad_all(self, dLoss_dJ=None, dLoss_dZc=None):
+        """Gradients of every device in one persistent launch (kmc_batch_grad_all)."""
+        return kmc_batch_grad_all(self.h, self.shapes, self.t, dLoss_dJ, dLoss_dZc)
 
     def grad(self, inst: int, dLoss_dJ: Optional[np.ndarray] = None,
              dLoss_dZc: Optional[np.ndarray] = None):

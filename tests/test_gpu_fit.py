@@ -45,6 +45,25 @@ def test_batch_gradient_equals_single_device_gradient(kmc):
     b.close()
 
 
+def test_batched_gradient_passes_equal_per_device_passes(kmc):
+    """kmc_batch_grad_all (one launch for all devices) returns, bit for bit,
+    each device's own kmc_batch_grad, with weights missing for some devices."""
+    devs, V, fills, samples = W.fit_batch(6, seed=4, n_pulses=2, forget_steps=1000)
+    devs = [dataclasses.replace(d, R=d.R // 16, L=d.L // 2) for d in devs]
+    devs[1] = dataclasses.replace(devs[1], electrodes=1, k_e=2e5, rho_e=0.2)
+    n = len(V)
+    b = kmc.Batch(devs, [V] * len(devs), [1] * len(devs), fills=fills)
+    b.step_n(n)
+    rng = np.random.default_rng(1)
+    wJs = [rng.normal(size=n) if i != 2 else None for i in range(len(devs))]
+    wZs = [rng.normal(size=(n, d.Z)) if i != 4 else None for i, d in enumerate(devs)]
+    g, se = b.grad_all(wJs, wZs)
+    for i in range(len(devs)):
+        gi, si = b.grad(i, wJs[i], wZs[i])
+        assert np.array_equal(g[i], gi, equal_nan=True) and np.array_equal(se[i], si, equal_nan=True), i
+    b.close()
+
+
 def _fit_case():
     """4 devices of 8,192 rails x 160 sites, 4 pulses + 4,000 steps; targets are
     the oracle's curves at the hidden (0.42 eV, 0.9) from 32 rails per device."""
