@@ -18,6 +18,7 @@ sample of the same device (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -497,6 +498,62 @@ def run_adjoint(args):
     return 0
 
 
+def run_stdp(args):
+    """STDP curve of the batched devices: the 512 spike-pair devices over their
+    whole 120 ms window in one batched run (rail counts divided by
+    --stdp-rail-div to bound the time; the rails are independent, so this
+    changes only the ensemble size), and per device the conductance change
+    dG = G(end) - G(just before the pre pulse), G = decile-1 ions / ions."""
+    import torch
+    from paper_2511_09413_gb300 import kmc
+
+    torch.cuda.set_device(0)
+    kmc.load()
+    devs, Vs, fills, delays = W.stdp_batch(args.instances)
+    div = max(1, args.stdp_rail_div)
+    devs = [dataclasses.replace(d, R=max(16, d.R // div)) for d in devs]
+    n = len(Vs[0])
+    t_pre = int(round(55.0 * 2000))
+    stream = torch.cuda.current_stream()
+    b = kmc.Batch(devs, Vs, [1] * len(devs), fills=fills, stream=stream.cuda_stream)
+    b.set_launch(8, 1024)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step_n(n - 1)
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    dG = np.zeros(len(devs))
+    for i in range(len(devs)):
+        _, Zc = b.traces(i)
+        N = float(Zc[0].sum())
+        dG[i] = (Zc[-1, 0] - Zc[t_pre, 0]) / max(N, 1.0)
+    b.close()
+    delays = np.asarray(delays)
+    edges = np.linspace(-50, 50, 11)
+    curve = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        m = (delays >= lo) & (delays < hi)
+        curve.append({"dt_ms": [float(lo), float(hi)], "devices": int(m.sum()),
+                      "dG_mean": float(dG[m].mean()) if m.any() else None,
+                      "dG_sem": float(dG[m].std(ddof=1) / np.sqrt(m.sum())) if m.sum() > 1 else None})
+    sites = sum(d.R * d.L for d in devs)
+    line = {
+        "metric": METRIC + ", batched STDP curve", "value": sites * (n - 1) / secs, "unit": UNIT,
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * secs, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "stdp_batch", "devices": len(devs), "sites_total": sites,
+                   "rail_divisor": div, "time_steps": n - 1,
+                   "protocol": "spike pair, 1 V 1 ms pulses, t_pre = 55 ms, 2000 steps/ms",
+                   "dG": "G(120 ms) - G(55 ms^-), G = decile-1 ions / ions"},
+        "stdp_curve": curve,
+        "per_device": {"dt_ms": delays.round(3).tolist(), "dG": dG.round(6).tolist()},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fit(args):
     """Batched + adjoint fit: gradient descent on (Ea, kappa) for 256 devices
     of 2,048-8,192 rails x 256-1,024 sites under a potentiation/forgetting
@@ -557,8 +614,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["kmc", "reference"], default="kmc")
-    ap.add_argument("--workload", choices=["hysteresis", "batched", "adjoint", "fit"],
+    ap.add_argument("--workload", choices=["hysteresis", "batched", "adjoint", "fit", "stdp"],
                     default="hysteresis")
+    ap.add_argument("--stdp-rail-div", type=int, default=16, help="stdp: rails divided by this")
     ap.add_argument("--fit-devices", type=int, default=256)
     ap.add_argument("--fit-pulses", type=int, default=8)
     ap.add_argument("--fit-forget", type=int, default=8000)
@@ -587,6 +645,8 @@ def main(argv=None):
         return run_adjoint(args)
     if args.workload == "fit":
         return run_fit(args)
+    if args.workload == "stdp":
+        return run_stdp(args)
     return run_kmc(args)
 
 
