@@ -526,9 +526,10 @@ def run_stdp(args):
     secs = e0.elapsed_time(e1) / 1e3
     dG = np.zeros(len(devs))
     for i in range(len(devs)):
-        _, Zc = b.traces(i)
-        N = float(Zc[0].sum())
-        dG[i] = (Zc[-1, 0] - Zc[t_pre, 0]) / max(N, 1.0)
+        _, Zp = b.traces(i, t_pre, 1)           # zone counts at the start of the pre pulse
+        _, Ze = b.traces(i, n - 2, 1)           # ... and at the start of the last step
+        N = float(Zp[0].sum())
+        dG[i] = (Ze[0, 0] - Zp[0, 0]) / max(N, 1.0)
     b.close()
     delays = np.asarray(delays)
     edges = np.linspace(-50, 50, 11)
