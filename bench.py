@@ -153,9 +153,42 @@ def cpu_baseline(wl, budget_s: float, stride: int = 16, steps_per_call: int = 25
         if el >= budget_s:
             break
     su = len(ids) * wl.device.L * steps
-    return {"value": su / el, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    # the same oracle on one core, on every 16th rail of that sample, ~1/4 of the budget
+    ids1 = ids[::16]
+    n_all = oracle.max_threads()
+    occ1 = oracle.init_occupancy(wl.device, 1, fill=wl.fill, rail_ids=ids1)
+    Ea1 = wl.Ea_site[ids1] if wl.Ea_site is not None else None
+    sim1 = oracle.OracleSim(wl.device, wl.V, occ1, Ea1, rail_ids=ids1, nthreads=1)
+    t1 = time.perf_counter()
+    steps1 = 0
+    while time.perf_counter() - t1 < budget_s / 4:
+        sim1.step_n(steps_per_call)
+        steps1 += steps_per_call
+    el1 = time.perf_counter() - t1
+    sim1.nthreads = n_all          # restore the thread count for later oracle calls
+    sim1.step_n(0)
+    return {"value": su / el, "unit": UNIT, "cores": n_all, "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": "%d of %d rails (every %dth) x %d steps of %s, %.1f s" % (
-                len(ids), wl.device.R, stride, steps, wl.name, el)}
+                len(ids), wl.device.R, stride, steps, wl.name, el),
+            "one_core": {"value": len(ids1) * wl.device.L * steps1 / el1, "unit": UNIT,
+                         "sample": "%d rails x %d steps, %.1f s" % (len(ids1), steps1, el1)}}
+
+
+def _cpu_model() -> str:
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return ln.split(":", 1)[1].strip()
+        with open("/proc/cpuinfo") as f:
+            parts = [ln.split(":", 1)[1].strip() for ln in f
+                     if ln.split(":")[0].strip() in ("CPU implementer", "CPU part")][:2]
+        return "%s (%s)" % (platform.machine(), ", ".join(parts))
+    except Exception:
+        return platform.machine()
 
 
 def run_reference(args):
