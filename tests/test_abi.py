@@ -98,6 +98,16 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.kmc_observables(None, 0, 0, None, None, None) == kmc.KMC_E_ARG
     assert lib.kmc_current_step(None) == -1
     lib.kmc_destroy(None)
+    g = (ctypes.c_double * 4)()
+    assert lib.kmc_grad(None, None, None, g, None) == kmc.KMC_E_ARG
+    assert lib.kmc_batch_grad(None, 0, None, None, g, None) == kmc.KMC_E_ARG
+    assert lib.kmc_batch_grad_all(None, None, None, g, None) == kmc.KMC_E_ARG
+    assert lib.kmc_batch_step_n(None, 1) == kmc.KMC_E_ARG
+    assert lib.kmc_set_accept_path(None, 1) == kmc.KMC_E_ARG
+    assert lib.kmc_philox_probe(None, None) == kmc.KMC_E_ARG
+    assert lib.kmc_batch_current_step(None) == -1
+    lib.kmc_batch_destroy(None)
+    assert len(lib.kmc_last_error()) > 0
 
 
 def test_missing_library_raises(tmp_path):
