@@ -94,7 +94,7 @@ int build_items(kmc_batch *b, int warps)
         const int G = 32 / lpr;
         const int64_t tile = (int64_t)G * warps;
         smem = std::max(smem, sweep_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, warps, b->flush,
-                                               b->dev[i]->P0site != nullptr, acc != 0));
+                                               acc != 0));
         for (int64_t r0 = 0; r0 < p.n_rails; r0 += tile) {
             BatchItem it;
             it.inst = (int32_t)i;

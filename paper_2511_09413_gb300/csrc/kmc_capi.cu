@@ -125,17 +125,16 @@ int pick_launch(kmc_handle *h)
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (max_smem <= 0) max_smem = 48 * 1024;
     max_smem = std::min(max_smem, 200 * 1024);
-    const bool ps = h->P0site != nullptr;
     l.acc = h->accept_req >= 0 ? h->accept_req : (h->args.P0f_scalar >= kAcceptAutoP0 ? 1 : 0);
     const bool acc = l.acc != 0;
-    while (warps > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps,
+    while (warps > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush,
                                          acc) > (size_t)max_smem)
         warps >>= 1;
-    while (flush > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps,
+    while (flush > 1 && sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush,
                                          acc) > (size_t)max_smem)
         flush >>= 1;
     l.warps = warps;
-    l.smem = sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, ps, acc);
+    l.smem = sweep_smem_bytes(l.lpr, l.wpl, p.n_zones, p.n_sites, warps, flush, acc);
     const int64_t rails_per_cta = (int64_t)G * warps;
     l.grid = (int)((p.n_rails + rails_per_cta - 1) / rails_per_cta);
     h->launch = l;

@@ -120,8 +120,7 @@ struct SweepLaunch {
 // (Eq. 1 at the device's mean barrier) is at least this large.
 constexpr double kAcceptAutoP0 = 1.0 / 128.0;
 
-size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite,
-                        bool acc);
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool acc);
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();

@@ -215,13 +215,13 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     l.acc = P0 >= kAcceptAutoP0 ? 1 : 0;
     const bool acc = l.acc != 0;
     while (warps > 1 &&
-           sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false, acc) > (size_t)max_smem)
+           sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, acc) > (size_t)max_smem)
         warps >>= 1;
     while (flush > 1 &&
-           sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false, acc) > (size_t)max_smem)
+           sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, acc) > (size_t)max_smem)
         flush >>= 1;
     l.warps = warps;
-    l.smem = sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, false, acc);
+    l.smem = sweep_smem_bytes(l.lpr, l.wpl, Z, L, warps, flush, acc);
     const int64_t rails_per_cta = (int64_t)(32 / l.lpr) * warps;
     l.grid = (int)((R + rails_per_cta - 1) / rails_per_cta);
     a.flush = flush;

@@ -125,7 +125,7 @@ struct Layout {
     // variable part: rm [G Z + 2 G] (zones, then the two electrode sites of each
     // rail): uint2 reject-sure bounds (R, L) on the draw's high word, or, with the
     // accept tables, uint4 (reject R, reject L, accept R, accept L), zf and P0b float2 [G][Z] (gz8 = align16(8 G Z) bytes each),
-    // Pb int [G][Z+1], then P0f float [G][32 LPR WPL] (per-site mode only)
+    // Pb int [G][Z+1]
     __host__ __device__ static size_t rm_bytes(int Z, bool acc)
     {
         return align16((size_t)(acc ? 16 : 8) * G * (Z + 2));
@@ -134,10 +134,9 @@ struct Layout {
     // Pb int [G][Z+1], then the zone counts last written to the trace int [G][Z]
     __host__ __device__ static size_t pb_only(int Z) { return align16((size_t)4 * G * (Z + 1)); }
     __host__ __device__ static size_t pb_bytes(int Z) { return pb_only(Z) + align16((size_t)4 * G * Z); }
-    __host__ __device__ static size_t bytes(int Z, bool persite, bool acc)
+    __host__ __device__ static size_t bytes(int Z, bool acc)
     {
-        return FIXED + rm_bytes(Z, acc) + 2 * gz8(Z) + pb_bytes(Z) +
-               (persite ? align16((size_t)4 * 1024 * WPL) : 0);
+        return FIXED + rm_bytes(Z, acc) + 2 * gz8(Z) + pb_bytes(Z);
     }
     // gradient pass, appended: accepted-trial masks accR, accL uint32 [W] each;
     // per (rail, zone) (gzq = align16(8 G Z) bytes per double): Q_z double,
@@ -161,7 +160,7 @@ struct WarpSmem {
     uint32_t gz;    // Layout::gz8(Z)
     uint32_t pbz;   // Layout::pb_bytes(Z)
     uint32_t npo;   // offset of the zone counts last written to the trace
-    uint32_t goff;  // Layout::bytes(Z, persite, acc): start of the gradient-pass region
+    uint32_t goff;  // Layout::bytes(Z, acc): start of the gradient-pass region
     uint32_t gzq;   // align16(8 G Z)
     __device__ uint32_t *mvR() const { return (uint32_t *)(b + Ly::MVR); }
     __device__ uint32_t *mvL() const { return (uint32_t *)(b + Ly::MVL); }
@@ -182,7 +181,6 @@ struct WarpSmem {
     __device__ float2 *zf() const { return (float2 *)(b + Ly::FIXED + rz); }
     __device__ float2 *P0b() const { return (float2 *)(b + Ly::FIXED + rz + gz); }
     __device__ int32_t *Pb() const { return (int32_t *)(b + Ly::FIXED + rz + 2 * gz); }
-    __device__ float *P0f() const { return (float *)(b + Ly::FIXED + rz + 2 * gz + pbz); }
     __device__ int32_t *Np() const { return (int32_t *)(b + npo); }
     __device__ uint32_t *accR() const { return (uint32_t *)(b + goff); }
     __device__ uint32_t *accL() const { return (uint32_t *)(b + goff + align16(4 * Ly::W)); }
@@ -272,7 +270,7 @@ __device__ __forceinline__ int bounded(uint32_t h, float p, float flo, float fhi
 template <int LPR, int WPL>
 __device__ __forceinline__ Decision decide(const WarpSmem<LPR, WPL> &S, const SweepArgs *g,
                                            uint4 x, int site, int g2, int z, bool isE,
-                                           bool persite, float flo, float fhi)
+                                           bool persite, float flo, float fhi, int64_t r2)
 {
     const int L = g->L, Z = g->Z;
     Decision D;
@@ -289,8 +287,10 @@ __device__ __forceinline__ Decision decide(const WarpSmem<LPR, WPL> &S, const Sw
     const float sR = bi.y * bi.x, sL = bi.y;
     D.kindR = 0;
     D.kindL = 0;
-    // base probability of each trial: P0 (scalar or this site's), or electrode exchange
-    float bR = persite ? S.P0f()[g2 * (32 * LPR * WPL) + site] : g->K->P0f;
+    // base probability of each trial: P0 (scalar or this site's), or electrode
+    // exchange.  The slow path is rare, so a site's P0 is read from global memory
+    // (rail r2) rather than staged in shared memory.
+    float bR = persite ? __ldg(g->P0f + r2 * L + site) : g->K->P0f;
     float bL = bR;
     if (isE) {
         if (!D.occd) {              // injection: site 0 via the right draw, L-1 via the left
@@ -362,7 +362,7 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
                           : make_uint4(0u, xy, 0u, xw);
     const int z = zone_tab[site];
     const bool isE = i >= n_inner;
-    Decision D = decide<LPR, WPL>(S, g, x, site, g2, z, isE, persite, flo, fhi);
+    Decision D = decide<LPR, WPL>(S, g, x, site, g2, z, isE, persite, flo, fhi, (int64_t)r2);
     const bool undecided = D.dR == 2 || D.dL == 2;
     if (!exact) {
         if (undecided) {
@@ -585,7 +585,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                                            int flush, int64_t tile_rail0, uint8_t *smem)
 {
     constexpr int G = 32 / LPR;
-    constexpr int LSEG = 32 * LPR * WPL;  // site capacity of one rail slot
     constexpr int VWIN = 32;              // steps per voltage window of the FP32 bounds
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -603,7 +602,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     const int nact = (int)max((int64_t)0, min((int64_t)G, (int64_t)a.R - rail0));
 
     using Ly = Layout<LPR, WPL>;
-    const size_t wb0 = Ly::bytes(Z, persite, ACC);
+    const size_t wb0 = Ly::bytes(Z, ACC);
     const size_t wb = wb0 + (GRAD ? Ly::grad_bytes(Z) : 0);
     WarpSmem<LPR, WPL> S;
     S.b = smem + (size_t)warp * wb;
@@ -670,11 +669,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         for (int pi = lane; pi < G * Z; pi += 32) {
             const int64_t r2 = rail0 + pi / Z;
             S.P0b()[pi] = r2 < a.R ? a.P0bnd[r2 * Z + pi % Z] : make_float2(0.0f, 0.0f);
-        }
-        for (int q = lane; q < G * L; q += 32) {
-            const int g2 = q / L, k = q - g2 * L;
-            const int64_t r2 = rail0 + g2;
-            S.P0f()[g2 * LSEG + k] = r2 < a.R ? a.P0f[r2 * L + k] : 0.0f;
         }
     }
 
@@ -1234,9 +1228,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
 }
 
 template <int LPR, int WPL, bool ACC>
-// 80 registers (3 CTAs of 256 threads per SM): the draw loop fits; the exact
-// FP64 path, which runs for about one draw in a million, may spill.
-__global__ void __launch_bounds__(256, 3) sweep_kernel(const SweepArgs a)
+// 64 registers (4 CTAs of 256 threads, 32 warps per SM): the kernel is bound
+// by instruction latency more than by any one pipe, and the extra resident
+// warps outweigh the spills (mostly on the slow and exact paths) that the cap
+// causes; with 80 registers and 3 CTAs it runs about 3 % slower.
+__global__ void __launch_bounds__(256, 4) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);
@@ -1459,29 +1455,29 @@ __global__ void __launch_bounds__(256) philox_probe_kernel(int iters, uint32_t k
 
 }  // namespace
 
-size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool persite, bool acc)
+size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool acc)
 {
     size_t wb = 0;
-    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, persite, acc);
-    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, persite, acc);
-    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, persite, acc);
-    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, persite, acc);
-    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, persite, acc);
-    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, persite, acc);
-    else wb = Layout<32, 1>::bytes(Z, persite, acc);
+    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, acc);
+    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, acc);
+    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, acc);
+    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, acc);
+    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, acc);
+    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, acc);
+    else wb = Layout<32, 1>::bytes(Z, acc);
     return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) + align16((size_t)L);
 }
 
 size_t grad_smem_bytes(int lpr, int wpl, int Z, int L, int warps)
 {
     size_t wb = 0;
-    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, false, true) + Layout<32, 2>::grad_bytes(Z);
-    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, false, true) + Layout<1, 1>::grad_bytes(Z);
-    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, false, true) + Layout<2, 1>::grad_bytes(Z);
-    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, false, true) + Layout<4, 1>::grad_bytes(Z);
-    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, false, true) + Layout<8, 1>::grad_bytes(Z);
-    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, false, true) + Layout<16, 1>::grad_bytes(Z);
-    else wb = Layout<32, 1>::bytes(Z, false, true) + Layout<32, 1>::grad_bytes(Z);
+    if (wpl == 2) wb = Layout<32, 2>::bytes(Z, true) + Layout<32, 2>::grad_bytes(Z);
+    else if (lpr == 1) wb = Layout<1, 1>::bytes(Z, true) + Layout<1, 1>::grad_bytes(Z);
+    else if (lpr == 2) wb = Layout<2, 1>::bytes(Z, true) + Layout<2, 1>::grad_bytes(Z);
+    else if (lpr == 4) wb = Layout<4, 1>::bytes(Z, true) + Layout<4, 1>::grad_bytes(Z);
+    else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, true) + Layout<8, 1>::grad_bytes(Z);
+    else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, true) + Layout<16, 1>::grad_bytes(Z);
+    else wb = Layout<32, 1>::bytes(Z, true) + Layout<32, 1>::grad_bytes(Z);
     return (size_t)warps * wb + align16((size_t)L);
 }
 
