@@ -40,10 +40,12 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kDeferCap = 64;           // deferred (exact-path) candidates per warp and step
 constexpr uint16_t kNoSite = 0xFFFFu;   // empty electrode slot of an inactive rail
-#ifndef KMC_DRAW_ILP
-#define KMC_DRAW_ILP 2
-#endif
-constexpr int kDrawIlp = KMC_DRAW_ILP;  // Philox blocks in flight per lane in the draw loop
+// Philox blocks in flight per lane per iteration of the draw loop: with the
+// accept tables each draw carries more state, and two blocks per lane at 4
+// CTAs per SM run fastest; the reject-only loop runs fastest with one block
+// per lane at 5 CTAs per SM (more resident warps instead of more ILP).
+constexpr int kDrawIlpAcc = 2;
+constexpr int kDrawIlpReject = 1;
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
 // multiplies; the high halves are xor-ed with the other counter words and the
@@ -952,17 +954,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             }
             __syncwarp();
 
-            // ---- 5. draws: two Philox blocks per lane per iteration; everything
-            //         but the reject-sure test is on the slow path
+            // ---- 5. draws: one or two Philox blocks per lane per iteration;
+            //         everything but the reject-sure (and, with ACC, the
+            //         accept-sure) test is on the slow path
             bool moved = false;
             if constexpr (ACC) {
-                for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlp) {
-                    uint32_t xy[kDrawIlp], xw[kDrawIlp];
-                    uint4 th[kDrawIlp];
-                    int sites[kDrawIlp], gs[kDrawIlp];
-                    bool at[kDrawIlp];
+                for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlpAcc) {
+                    uint32_t xy[kDrawIlpAcc], xw[kDrawIlpAcc];
+                    uint4 th[kDrawIlpAcc];
+                    int sites[kDrawIlpAcc], gs[kDrawIlpAcc];
+                    bool at[kDrawIlpAcc];
 #pragma unroll
-                    for (int q = 0; q < kDrawIlp; ++q) {
+                    for (int q = 0; q < kDrawIlpAcc; ++q) {
                         const int i = i0 + 32 * q;
                         const bool has = i < nlist;
                         const uint16_t d = S.list()[has ? i : i0];
@@ -979,7 +982,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         at[q] = has && (x.y <= th[q].x || x.w <= th[q].y);
                     }
 #pragma unroll
-                    for (int q = 0; q < kDrawIlp; ++q) {
+                    for (int q = 0; q < kDrawIlpAcc; ++q) {
                         if (!at[q]) continue;
                         const int i = i0 + 32 * q;
                         bool slow = i >= n_inner;   // electrode sites
@@ -1015,12 +1018,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     }
                 }
             } else {
-                for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlp) {
-                    // kDrawIlp independent Philox blocks per lane per iteration
-                    uint32_t xy[kDrawIlp], xw[kDrawIlp];
-                    bool at[kDrawIlp];
+                for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlpReject) {
+                    // kDrawIlpReject independent Philox blocks per lane per iteration
+                    uint32_t xy[kDrawIlpReject], xw[kDrawIlpReject];
+                    bool at[kDrawIlpReject];
     #pragma unroll
-                    for (int q = 0; q < kDrawIlp; ++q) {
+                    for (int q = 0; q < kDrawIlpReject; ++q) {
                         const int i = i0 + 32 * q;
                         const bool has = i < nlist;
                         const uint16_t d = S.list()[has ? i : i0];
@@ -1039,7 +1042,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         at[q] = has && (x.y <= rm.x || x.w <= rm.y);
                     }
     #pragma unroll
-                    for (int q = 0; q < kDrawIlp; ++q)
+                    for (int q = 0; q < kDrawIlpReject; ++q)
                         if (at[q])
                             moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
                                                               zone_tab, persite, flo, fhi, false, xy[q],
@@ -1228,11 +1231,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
 }
 
 template <int LPR, int WPL, bool ACC>
-// 64 registers (4 CTAs of 256 threads, 32 warps per SM): the kernel is bound
-// by instruction latency more than by any one pipe, and the extra resident
-// warps outweigh the spills (mostly on the slow and exact paths) that the cap
-// causes; with 80 registers and 3 CTAs it runs about 3 % slower.
-__global__ void __launch_bounds__(256, 4) sweep_kernel(const SweepArgs a)
+// 4 CTAs of 256 threads per SM (64 registers) with the accept tables, 5 (48
+// registers) without: the kernel is bound by instruction latency more than by
+// any one pipe, and the extra resident warps outweigh the spills (mostly on
+// the slow and exact paths) that the caps cause.  With 80 registers and 3 CTAs
+// the hysteresis device runs 4.5 % slower.
+__global__ void __launch_bounds__(256, ACC ? 4 : 5) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);
