@@ -221,6 +221,25 @@ def test_hysteresis_device_sampled_rails_full_size(kmc):
     sim.close()
 
 
+def test_hysteresis_device_sampled_rails_whole_protocol(kmc):
+    """The same device through its whole protocol (two +-2 V cycles, 2e5
+    steps, in the bench's 1,000-step launches): every 256th rail re-run on the
+    oracle matches at every 50,000-step checkpoint."""
+    wl = W.hysteresis_65536x1024(steps_per_cycle=100000, cycles=2)
+    n_total, chunk, launch = len(wl.V), 50000, 1000
+    assert n_total == 200000
+    sim = kmc.Sim.from_workload(wl)
+    ids = np.arange(0, wl.device.R, 256)
+    orc = oracle.OracleSim(wl.device, wl.V, sim.occupancy()[ids], wl.Ea_site[ids], rail_ids=ids)
+    for t in range(chunk, n_total + 1, chunk):
+        for _ in range(chunk // launch):
+            sim.step_n(launch)
+        orc.step_n(chunk)
+        assert np.array_equal(sim.occupancy()[ids], orc.occ), "rails differ by step %d" % t
+    assert orc.occ.sum() > 0
+    sim.close()
+
+
 @pytest.mark.parametrize("L,electrodes", [(128, 0), (40, 1), (1024, 1)])
 def test_rapidly_varying_bias_bit_exact(kmc, L, electrodes):
     # the bias jumps every step, so the FP32 bands must cover a wide voltage window
