@@ -39,7 +39,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kDeferCap = 64;           // deferred (exact-path) candidates per warp and step
-constexpr uint16_t kNoSite = 0xFFFFu;   // empty electrode slot of an inactive rail
 // Philox blocks in flight per lane per iteration of the draw loop: with the
 // accept tables each draw carries more state, and two blocks per lane at 4
 // CTAs per SM run fastest; the reject-only loop runs fastest with one block
@@ -55,10 +54,14 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        // one widening multiply per product (both halves at once): 1 % faster
+        // in the sweep and 2.5 % in the Philox-only probe than separate
+        // low and high multiplies
+        uint64_t p0, p1;
+        asm("mul.wide.u32 %0, %1, %2;" : "=l"(p0) : "r"(c0), "r"(0xD2511F53u));
+        asm("mul.wide.u32 %0, %1, %2;" : "=l"(p1) : "r"(c2), "r"(0xCD9E8D57u));
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c0 = hi1 ^ c1 ^ rk0[i];
         c1 = lo1;
         c2 = hi0 ^ c3 ^ rk1[i];
@@ -116,8 +119,7 @@ struct Layout {
     static constexpr size_t FR = MVL + align16(4 * W);
     static constexpr size_t FL = FR + align16(4 * W);
     static constexpr size_t OW = FL + align16(4 * W);
-    static constexpr size_t THRE = OW + align16(4 * W);        // uint4 [G][2]
-    static constexpr size_t INJ = THRE + align16(16 * 2 * G);  // int [2][G]
+    static constexpr size_t INJ = OW + align16(4 * W);         // int [2][G]
     static constexpr size_t N0S = INJ + align16(4 * 2 * G);    // int [G]
     static constexpr size_t FS = N0S + align16(4 * G);         // int [G]
     static constexpr size_t NDEF = FS + align16(4 * G);        // int [4]
@@ -169,7 +171,6 @@ struct WarpSmem {
     __device__ uint32_t *fR() const { return (uint32_t *)(b + Ly::FR); }
     __device__ uint32_t *fL() const { return (uint32_t *)(b + Ly::FL); }
     __device__ uint32_t *ow() const { return (uint32_t *)(b + Ly::OW); }
-    __device__ uint4 *thrE() const { return (uint4 *)(b + Ly::THRE); }
     __device__ int32_t *inj() const { return (int32_t *)(b + Ly::INJ); }
     __device__ int32_t *N0s() const { return (int32_t *)(b + Ly::N0S); }
     __device__ int32_t *Fs() const { return (int32_t *)(b + Ly::FS); }
