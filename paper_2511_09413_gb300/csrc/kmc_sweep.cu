@@ -39,11 +39,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kDeferCap = 64;           // deferred (exact-path) candidates per warp and step
-// Philox blocks in flight per lane per iteration of the draw loop: with the
-// accept tables each draw carries more state, and two blocks per lane at 4
-// CTAs per SM run fastest; the reject-only loop runs fastest with one block
-// per lane at 5 CTAs per SM (more resident warps instead of more ILP).
-constexpr int kDrawIlpAcc = 2;
+// Philox blocks in flight per lane per iteration of the draw loop.  One is
+// fastest on both loops: the kernel gains more from resident warps than from
+// ILP (the accept-table loop at 4 CTAs per SM, the reject-only loop at 5).
+constexpr int kDrawIlpAcc = 1;
 constexpr int kDrawIlpReject = 1;
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
@@ -955,9 +954,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             }
             __syncwarp();
 
-            // ---- 5. draws: one or two Philox blocks per lane per iteration;
-            //         everything but the reject-sure (and, with ACC, the
-            //         accept-sure) test is on the slow path
+            // ---- 5. draws: one Philox block per lane per iteration; everything
+            //         but the reject-sure (and, with ACC, the accept-sure) test
+            //         is on the slow path
             bool moved = false;
             if constexpr (ACC) {
                 for (int i0 = lane; i0 < nlist; i0 += 32 * kDrawIlpAcc) {
