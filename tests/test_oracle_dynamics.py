@@ -246,3 +246,36 @@ def test_rail_sample_matches_full_device():
     part.step_n(300)
     assert np.array_equal(part.occ, full.occ[ids])
     assert np.array_equal(part.J_rail, full.J_rail[ids])
+
+
+def _init_keys(dev, rails):
+    """64-bit placement keys (R5, R17): Philox4x32-10 block at counter
+    (site, rail, 0xFFFFFFFF, instance) under key (seed lo, seed hi), words
+    (x1:x0); the generator itself is pinned against cuRAND elsewhere."""
+    key = [dev["seed"] & 0xFFFFFFFF, dev["seed"] >> 32]
+    out = np.zeros((len(rails), dev["L"]), dtype=np.uint64)
+    for i, r in enumerate(rails):
+        for k in range(dev["L"]):
+            x = oracle.philox4x32_10([k, int(r), 0xFFFFFFFF, dev["instance"]], key)
+            out[i, k] = (np.uint64(x[1]) << np.uint64(32)) | np.uint64(x[0])
+    return out
+
+
+def test_placement_is_the_smallest_keys_and_the_bernoulli_rule():
+    dev = dict(R=5, L=13, Z=3, electrodes=0, d=1.0, dt=1e-9, T=300.0, Ea=0.40, nu=1e12,
+               alpha=0.2, kappa=1.0, k_e=0.0, rho_e=0.0, seed=0x1234_5678_9ABC_DEF1,
+               instance=7)
+    keys = _init_keys(dev, range(dev["R"]))
+    flat = keys.ravel()
+    for n in (0, 1, 17, 64, 65):
+        want = np.zeros(flat.size, dtype=np.uint8)
+        want[np.lexsort((np.arange(flat.size), flat))[:n]] = 1      # by key, ties by index
+        assert np.array_equal(oracle.init_occupancy(dev, 0, n_ions=n).ravel(), want)
+    for fill in (0.0, 0.3, 0.75, 1.0):
+        u = (keys >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        assert np.array_equal(oracle.init_occupancy(dev, 1, fill=fill), (u < fill).astype(np.uint8))
+    # a sample of rails (index map) draws the rails' own keys
+    ids = np.array([4, 0, 2], dtype=np.int32)
+    u = (_init_keys(dev, ids) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    assert np.array_equal(oracle.init_occupancy(dev, 1, fill=0.5, rail_ids=ids),
+                          (u < 0.5).astype(np.uint8))
