@@ -279,3 +279,28 @@ def test_placement_is_the_smallest_keys_and_the_bernoulli_rule():
     u = (_init_keys(dev, ids) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
     assert np.array_equal(oracle.init_occupancy(dev, 1, fill=0.5, rail_ids=ids),
                           (u < 0.5).astype(np.uint8))
+
+
+@pytest.mark.parametrize("electrodes", [0, 1])
+def test_per_step_trace_definitions(electrodes):
+    """Zone counts are those of each step's start occupancy (R16's trace);
+    with blocking electrodes the step's current is the drop of the summed
+    ion position over that step (each leftward crossing lowers it by one)."""
+    rng = np.random.default_rng(11 + electrodes)
+    dev = dict(R=12, L=47, Z=5, electrodes=electrodes, d=1.0, dt=5e-7, T=300.0, Ea=0.40,
+               nu=1e12, alpha=0.2, kappa=1.0, k_e=2e6 if electrodes else 0.0,
+               rho_e=0.3 if electrodes else 0.0, seed=21, instance=3)
+    occ = (rng.random((12, 47)) < 0.35).astype(np.uint8)
+    V = np.concatenate([np.linspace(0.0, 2.5, 20), np.linspace(2.5, -2.5, 40), np.zeros(20)])
+    sim = oracle.OracleSim(dev, V, occ)
+    z = np.array([oracle.zone_of(k, 47, 5) for k in range(47)])
+    k = np.arange(47)
+    moved = 0
+    for t in range(len(V)):
+        before = sim.occ.copy()
+        J, Zc = sim.step_n(1)
+        assert np.array_equal(Zc[0], np.bincount(z, weights=before.sum(axis=0), minlength=5))
+        if electrodes == 0:
+            assert J[0] == (before * k).sum() - (sim.occ.astype(np.int64) * k).sum()
+        moved += int(np.any(before != sim.occ))
+    assert moved > len(V) // 2
