@@ -304,3 +304,38 @@ def test_per_step_trace_definitions(electrodes):
             assert J[0] == (before * k).sum() - (sim.occ.astype(np.int64) * k).sum()
         moved += int(np.any(before != sim.occ))
     assert moved > len(V) // 2
+
+
+def test_single_ion_follows_its_own_draws_exactly():
+    """One ion, no space charge, blocking walls: each step its right trial
+    uses u = ((x1:x0) >> 11) 2^-53 and its left trial ((x3:x2) >> 11) 2^-53
+    of the Philox block at counter (site, rail, step, instance) (R5, R6); it
+    moves right iff only the right trial is accepted, left iff only the left
+    one is, and stays if both or neither are (R2); trials into a wall are not
+    made (R14).  Checked move by move against the oracle."""
+    L, V, T, dt = 6, 0.3, 300.0, 2e-6
+    dev = dict(R=1, L=L, Z=2, electrodes=0, d=1.0, dt=dt, T=T, Ea=0.40, nu=1e12,
+               alpha=0.2, kappa=0.0, k_e=0.0, rho_e=0.0, seed=0xC0FFEE, instance=9)
+    P0 = -np.expm1(-2.0 * 1e12 * np.exp(-0.40 / (8.6173e-5 * T)) * dt)
+    B = np.exp(-(V / L) / (8.6173e-5 * T))          # Eqs. 3-4, t_dev = L d
+    pL = P0 / (1.0 + B)                              # Eq. 5
+    pR = pL * B                                      # Eq. 6
+    occ = np.zeros((1, L), dtype=np.uint8)
+    occ[0, 2] = 1
+    n = 400
+    sim = oracle.OracleSim(dev, np.full(n, V), occ)
+    key = [0xC0FFEE, 0]
+    pos, kinds = 2, set()
+    for t in range(n):
+        x = [int(w) for w in oracle.philox4x32_10([pos, 0, t, 9], key)]
+        uR = ((x[1] << 32 | x[0]) >> 11) * 2.0 ** -53
+        uL = ((x[3] << 32 | x[2]) >> 11) * 2.0 ** -53
+        aR = pos < L - 1 and uR <= pR
+        aL = pos > 0 and uL <= pL
+        step = (1 if aR else 0) - (1 if aL else 0)
+        kinds.add((aR, aL))
+        J, _ = sim.step_n(1)
+        pos += step
+        assert sim.occ[0, pos] == 1 and sim.occ.sum() == 1, "step %d" % t
+        assert J[0] == -step
+    assert kinds == {(False, False), (True, False), (False, True), (True, True)}
