@@ -2,9 +2,15 @@
  * kmc_oracle.c -- plain FP64 CPU oracle of the rail-based kinetic Monte Carlo
  * ion-migration step (arXiv 2511.09413, Supplementary Information S2.1).
  *
- * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
- * CPU-baseline leg of bench.py may load this library.  It shares no code,
- * header, table or constant generator with the CUDA path.
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
+ * bench.py's CPU-baseline leg and reference arm (--impl reference) may load
+ * this library.  It shares no code, header, table or constant generator with
+ * the CUDA path.
+ *
+ * Parity unpinned: the magnitude of the space-charge coupling (alpha, kappa
+ * below).  The paper prints no value or figure data that fixes it; its
+ * structure (zero for a uniform rail, the Dirichlet constraint, the discrete
+ * Gauss law, mirror symmetry, the sign of the response) is pinned.
  *
  * The method is a stochastic iteration, so the oracle is the algorithm itself
  * written out step by step: one loop per step, per rail, per site, in FP64,

@@ -1,7 +1,8 @@
 """ctypes front end of the FP64 C oracle (kmc_oracle.c).
 
-Test infrastructure only: it builds and loads ``liboracle.so`` from the C
-source next to it.  Every function here is a thin marshalling wrapper; the
+Test infrastructure only (tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline leg and reference arm): it builds and loads ``liboracle.so``
+from the C source next to it.  Every function here is a thin marshalling wrapper; the
 arithmetic of the method is in kmc_oracle.c.
 """
 from __future__ import annotations
