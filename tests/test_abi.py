@@ -119,3 +119,24 @@ def test_missing_library_raises(tmp_path):
             kmc.load(str(tmp_path / "libkmc.so"))
     finally:
         kmc._lib = saved
+
+
+def test_device_maps_to_the_same_quantities_on_both_sides():
+    """A workloads.Device reaches the C ABI (kmc_params) and the oracle
+    (OrcParams) as the same physical quantities, field by field."""
+    import oracle
+    from paper_2511_09413_gb300 import kmc, workloads as W
+    dev = W.Device(R=7, L=33, Z=5, electrodes=1, d=0.7, dt=3e-7, T=310.0, Ea=0.37, nu=2e12,
+                   alpha=0.15, kappa=0.8, k_e=4e6, rho_e=0.35, seed=-5, instance=11, rule=1)
+    p = kmc.params_from_device(dev, init_mode=1, fill=0.3)
+    q = oracle.params(dev)
+    pairs = [("n_rails", "R"), ("n_sites", "L"), ("n_zones", "Z"), ("electrodes", "electrodes"),
+             ("site_spacing_nm", "d"), ("dt_s", "dt"), ("T_K", "T"), ("Ea_eV", "Ea"),
+             ("nu_Hz", "nu"), ("alpha_V", "alpha"), ("kappa", "kappa"),
+             ("k_electrode_Hz", "k_e"), ("rho_electrode", "rho_e"), ("seed", "seed"),
+             ("instance", "instance"), ("update_rule", "rule")]
+    for a, b in pairs:
+        assert getattr(p, a) == getattr(q, b), (a, b)
+        assert getattr(q, b) == {"seed": (-5) & 0xFFFFFFFFFFFFFFFF}.get(b, dev.as_dict()[b])
+    assert p.init_mode == 1 and p.fill == 0.3 and p.reserved == 0
+    assert kmc.params_from_device(dev.as_dict(), init_mode=0, n_ions=9).n_ions == 9
