@@ -4,14 +4,19 @@ Workload (N=1): the plain large device -- 65,536 rails x 1,024 sites (64 MiB
 uint8 occupancy), 25 % Bernoulli filling, per-site barriers Ea ~ N(0.40, 0.02)
 eV, T = 300 K, injecting/extracting electrodes (1e9 Hz), triangular +-2 V sweep
 with 1e5 steps per cycle.  One benchmark step = one kmc_step_n call advancing
-every rail and site by `--chunk` time steps (default 1,000), so one step is
-R * L * chunk site-updates.
+every rail and site by `--chunk` time steps (default 10,000), so one step is
+R * L * chunk site-updates; the default 20 timed steps cover two whole cycles
+of the sweep (every phase of the protocol equally), and the end-to-end leg
+times the next 20.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kmc|reference]
+                    [--scaling weak|strong]
 
-Under torchrun (N > 1) every rank advances its own independent device instance
-(instance = rank, weak scaling, no collective on the data path); the timed
-region is bracketed by a barrier and the maximum over ranks is reported.
+Under torchrun (N > 1) the device is partitioned by rails (rail_base, no
+collective on the data path): with --scaling weak (the default) every rank
+advances its own 65,536 rails of a device of N x 65,536 rails; with
+--scaling strong the ranks split the 65,536 rails.  The timed region is
+bracketed by a barrier and the maximum over ranks is reported.
 ``--impl reference`` times the FP64 CPU oracle on this host's cores on a bounded
 sample of the same device (rank 0 only).
 """
@@ -38,7 +43,13 @@ from paper_2511_09413_gb300 import workloads as W  # noqa: E402
 METRIC = "site-updates/s on 1 GB300 (% HBM roofline)"
 UNIT = "site-updates/s"
 BYTES_PER_SITE_UPDATE = 2.0        # uint8 read + write per site and step
-PHILOX_IMAD = 40                   # IMAD-pipe ops per Philox4x32-10 block: 20 products x (hi, lo)
+# IMAD-pipe issue slots per Philox4x32-10 block of one lane whose rail, step and
+# instance counter words are warp-uniform: rounds 1 and 2 multiply one per-lane
+# word each (the other product is warp-uniform), rounds 3-9 two, round 10 two
+# low halves only (its high halves feed words the draw does not use); a
+# 32x32->64 widening multiply takes two of the pipe's slots, a low half one:
+# 16 x 2 + 2 = 34.
+PHILOX_IMAD_SLOTS = 34
 IMAD_PER_SM_PER_CLK = 64           # 32-bit integer multiply-add lanes per SM per clock
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -53,11 +64,12 @@ def _peaks():
         return 6800.0, "fallback", SM_MAX_MHZ
 
 
-def _traffic_per_launch(rails: int):
+def _traffic_per_launch(rails: int, steps: int):
     """DRAM bytes (read + write) of one sweep launch from the ncu capture in
     profiles/sweep_traffic.json, scaled to `rails` (the per-launch traffic is
     the occupancy and per-site tables, proportional to rails x sites), or None
-    when the kernel source changed since the capture."""
+    when the kernel source changed since the capture or the capture's launch
+    covered another number of steps."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
@@ -66,7 +78,7 @@ def _traffic_per_launch(rails: int):
             sha = hashlib.sha256(f.read()).hexdigest()
     except Exception:
         return None
-    if sha != rec.get("kernel_source_sha256"):
+    if sha != rec.get("kernel_source_sha256") or rec.get("steps_per_launch") != steps:
         return None
     return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * rails / rec["rails"]
 
@@ -244,19 +256,27 @@ def run_kmc(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     kmc.load()
     stream = torch.cuda.current_stream()
-    n_needed = (args.warmup + args.steps) * args.chunk + 2 * args.chunk
-    wl = W.hysteresis_65536x1024(R=args.rails, steps_per_cycle=100000, cycles=2)
-    wl.V = _voltage(n_needed)
-    wl.device.instance = MG.shard_instances(world, rank, world)[0]   # one instance per rank
+    chunk = args.chunk
+    # rails of this rank: its own 65,536 of a device of world x 65,536 (weak),
+    # or its part of the 65,536 (strong); the rail index is global either way
+    if args.scaling == "strong":
+        r0, r1 = MG.shard_rails(args.rails, rank, world)
+    else:
+        r0, r1 = rank * args.rails, (rank + 1) * args.rails
+    # warm-up, timed and end-to-end steps, and one chunk of slack
+    n_needed = (args.warmup + 2 * args.steps + 1) * chunk
+    cycles = max(2, -(-n_needed // 100000))
+    wl = W.hysteresis_65536x1024(R=r1 - r0, rail_base=r0, steps_per_cycle=100000, cycles=cycles)
     sim = kmc.Sim.from_workload(wl, stream=stream.cuda_stream)
     R, L = wl.device.R, wl.device.L
-    su_per_step = R * L * args.chunk
+    su_per_step = R * L * chunk
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
-        sim.step_n(args.chunk)
+        sim.step_n(chunk)
     torch.cuda.synchronize()
     cnt0 = sim.counters()
+    t_first = sim.t
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -268,71 +288,93 @@ def run_kmc(args):
     for i in range(args.steps):
         flush_buf.zero_()                         # evict L2 between timed steps
         ev[i][0].record(stream)
-        sim.step_n(args.chunk)
+        sim.step_n(chunk)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     MG.barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    t_last = sim.t
     ms_steps = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(ms_steps)
+    ms_rank = sum(ms_steps)
     cnt1 = sim.counters()
-    ms = MG.max_over_ranks(ms, device="cuda")
-    value = MG.whole_job_rate([su_per_step * args.steps] * world, ms / 1e3)
+    ms = MG.max_over_ranks(ms_rank, device="cuda")
+    # site-updates of every rank in the timed region
+    if args.scaling == "strong":
+        units = [float((b - a) * L * chunk * args.steps)
+                 for a, b in (MG.shard_rails(args.rails, k, world) for k in range(world))]
+    else:
+        units = [float(args.rails * L * chunk * args.steps)] * world
+    value = MG.whole_job_rate(units, ms / 1e3)
 
-    # end to end through the C ABI with host buffers: voltage chunk in, traces out
+    # end to end through the C ABI with host buffers, over as many steps as
+    # the timed region: the step's voltage chunk in, its traces out
     from paper_2511_09413_gb300.kmc import kmc_observables, kmc_set_voltage
-    Vpin = torch.empty(args.chunk, dtype=torch.float64, pin_memory=True).numpy()
-    Jpin = torch.empty(args.chunk, dtype=torch.int64, pin_memory=True).numpy()
-    Zpin = torch.empty((args.chunk, wl.device.Z), dtype=torch.int64, pin_memory=True).numpy()
-    e2e_steps = max(1, min(args.steps, 5))
+    Vpin = torch.empty(chunk, dtype=torch.float64, pin_memory=True).numpy()
+    Jpin = torch.empty(chunk, dtype=torch.int64, pin_memory=True).numpy()
+    Zpin = torch.empty((chunk, wl.device.Z), dtype=torch.int64, pin_memory=True).numpy()
+    e2e_first = sim.t
     MG.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         first = sim.t
-        Vpin[:] = wl.V[first:first + args.chunk]
+        Vpin[:] = wl.V[first:first + chunk]
         kmc_set_voltage(sim.h, first, Vpin)
-        sim.step_n(args.chunk)
-        kmc_observables(sim.h, first, args.chunk, Jpin, Zpin, None)
+        sim.step_n(chunk)
+        kmc_observables(sim.h, first, chunk, Jpin, Zpin, None)
     torch.cuda.synchronize()
     e2e_s = MG.max_over_ranks(time.perf_counter() - t0, device="cuda")
-    e2e_value = MG.whole_job_rate([su_per_step * e2e_steps] * world, e2e_s)
+    e2e_value = MG.whole_job_rate(units, e2e_s)
+    e2e_last = sim.t
 
     if rank == 0:
         hbm, hbm_src, sm_max = _peaks()
         draws = float(cnt1[0] - cnt0[0]) / args.steps        # Philox blocks per launch
-        per_launch_s = (ms / args.steps) / 1e3 if world == 1 else (sum(ms_steps) / args.steps) / 1e3
-        sm_mhz = clk.get("sm_mhz") or sm_max
-        alu_peak = SMS * IMAD_PER_SM_PER_CLK * sm_max * 1e6 / PHILOX_IMAD / 1e9   # G blocks/s
+        per_launch_s = (ms_rank / args.steps) / 1e3
+        alu_peak = SMS * IMAD_PER_SM_PER_CLK * sm_max * 1e6 / PHILOX_IMAD_SLOTS / 1e9  # G blocks/s
         achieved = draws / per_launch_s / 1e9
         from paper_2511_09413_gb300.kmc import kmc_philox_probe
         probe = kmc_philox_probe(stream.cuda_stream) / 1e9
+        hbm_achieved = BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9
+        cyc = (t_last - t_first) / 100000.0
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": wl.name, "rails": R, "sites": L, "time_steps_per_step": args.chunk,
-                       "site_updates_per_step": su_per_step, "fill": wl.fill,
+            "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name if world == 1 else "hysteresis_%dx%d" % (
+                           args.rails * (world if args.scaling == "weak" else 1), L),
+                       "rails": R * world if args.scaling == "weak" else args.rails,
+                       "rails_per_gpu": R, "sites": L,
+                       "time_steps_per_step": chunk, "site_updates_per_step": su_per_step * world
+                       if args.scaling == "weak" else args.rails * L * chunk,
+                       "timed_time_steps": [t_first, t_last],
+                       "timed_protocol_cycles": cyc,
+                       "e2e_time_steps": [e2e_first, e2e_last],
+                       "fill": wl.fill,
                        "electrodes": "injecting/extracting 1e9 Hz", "barriers": "per site N(0.40, 0.02) eV",
-                       "protocol": "triangle +-2 V, 1e5 steps/cycle", "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": "one independent device per GPU" if world > 1 else "single GPU"},
+                       "protocol": "triangle +-2 V, 1e5 steps/cycle",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": ("rails partitioned over %d GPUs (rail_base), %s scaling" % (
+                           world, args.scaling)) if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "G Philox4x32-10 blocks/s", "frac": achieved / alu_peak,
-                         "traffic": _traffic_per_launch(R),
+                         "traffic": _traffic_per_launch(R, chunk),
                          "traffic_unit": "DRAM bytes per launch (ncu, scaled by rails)",
-                         "peak_basis": "%d SMs x %d IMAD lanes/clk x %.0f MHz / %d IMAD ops per block" % (
-                             SMS, IMAD_PER_SM_PER_CLK, sm_max, PHILOX_IMAD),
-                         "philox_only_probe": {"achieved": probe, "frac": achieved / probe,
+                         "peak_basis": "%d SMs x %d IMAD lanes/clk x %.0f MHz / %d IMAD issue slots "
+                                       "per block" % (SMS, IMAD_PER_SM_PER_CLK, sm_max,
+                                                      PHILOX_IMAD_SLOTS),
+                         "philox_only_probe": {"achieved": probe, "frac_of_peak": probe / alu_peak,
+                                               "sweep_frac_of_probe": achieved / probe,
                                                "basis": "kmc_philox_probe: the draw loop's Philox "
                                                         "blocks alone, measured in this run"},
-                         "hbm_basis": {"achieved_GBps": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9,
+                         "hbm_basis": {"achieved_GBps": hbm_achieved,
                                        "peak_GBps": hbm, "peak_source": hbm_src,
-                                       "frac": BYTES_PER_SITE_UPDATE * su_per_step / per_launch_s / 1e9 / hbm,
+                                       "frac": hbm_achieved / hbm,
                                        "bytes_per_site_update": BYTES_PER_SITE_UPDATE}},
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "steps": args.steps,
                     "h2d_bytes_per_step": int(Vpin.nbytes),
                     "d2h_bytes_per_step": int(Jpin.nbytes + Zpin.nbytes)},
             "gpu_launches": args.steps,
@@ -662,7 +704,9 @@ def main(argv=None):
     ap.add_argument("--fd-replicas", type=int, default=32, help="adjoint: replicas of the FD check")
     ap.add_argument("--instances", type=int, default=512, help="devices in the batched workload")
     ap.add_argument("--probe", type=int, default=1024, help="autotuner probe steps (batched)")
-    ap.add_argument("--chunk", type=int, default=1000, help="time steps per benchmark step")
+    ap.add_argument("--chunk", type=int, default=10000, help="time steps per benchmark step")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="N > 1: each rank its own 65,536 rails (weak) or a share of them (strong)")
     ap.add_argument("--rails", type=int, default=65536)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -70,12 +70,19 @@ typedef struct kmc_params {
                                  bonds (b, b+1) with b = t mod 2 are active (the left
                                  electrode's bond is b = -1), each ion makes at most one
                                  trial, across its active bond, and no hops conflict    */
-    int32_t reserved;         /* 0                                                           */
+    int32_t rail_base;        /* global index of rail 0 of this device, >= 0 (default 0):
+                                 rail r draws with Philox counter word 1 = rail_base + r
+                                 and places its ions with that index, so a device of
+                                 n_rails rails starting at rail_base advances exactly
+                                 rows [rail_base, rail_base + n_rails) of a larger
+                                 device with the same seed and instance (rails are
+                                 independent, S1.2, S2.1.1).  rail_base + n_rails must
+                                 not exceed 2^31 - 1; init_mode 0 needs rail_base 0   */
 } kmc_params;
 
 /* One decision whose uniform fell within 1e-12 of its threshold. */
 typedef struct kmc_log_entry {
-    int32_t rail;
+    int32_t rail;   /* global rail index: rail_base + the rail's row in the device */
     uint32_t step;
     int32_t site;
     int32_t dir;  /* 0 right trial, 1 left trial */
@@ -109,18 +116,39 @@ int kmc_create(const kmc_params *params, const double *V_per_step, int64_t n_ste
                void *cuda_stream, kmc_handle **out);
 
 /* Advance n_steps >= 0 steps from the handle's current step (asynchronous on
- * the handle's stream).  KMC_E_RANGE if the voltage table is too short. */
+ * the handle's stream).  Each step is the synchronous sweep of S2.1.2 - S2.1.7
+ * over every rail and site: zone counts (S2.1.5), the space-charge field
+ * (S2.1.8) and the energy gap of Eq. 3, the Boltzmann factor of Eq. 4, the hop
+ * probabilities of Eqs. 5-6 with the base probability from Eq. 1, two uniforms
+ * per ion compared with "u <= p" (S2.1.6 - S2.1.7), exclusion against the
+ * step-start occupancy, conflict cancellation, electrode exchange, and the
+ * net-crossing current.  The occupancy and traces stay on the device.
+ * KMC_E_RANGE if the voltage table is too short; KMC_E_CUDA if a launch fails. */
 int kmc_step_n(kmc_handle *h, int64_t n_steps);
 
 /* Read observables (synchronizes the stream):
  *  J_out[count]            net leftward bond crossings per step, all rails and
- *                          bonds including the electrode bonds (may be NULL);
+ *                          bonds including the electrode bonds (may be NULL):
+ *                          the ionic current of each step, counted exactly as
+ *                          the moves of S2.1.7 that cross a bond;
  *  zone_counts_out[count][Z] ions per zone at the start of each step, summed
- *                          over rails (may be NULL);
+ *                          over rails (may be NULL): with Z = 10 the deciles
+ *                          whose ion fractions the paper converts to
+ *                          conductance and current (S3: first decile at V > 0,
+ *                          tenth at V < 0; zones as in S2.1.5);
  *  occ_out_or_null[R][L]   current occupancy (may be NULL).
- * Steps [first_step, first_step + count) must already have been simulated. */
+ * Steps [first_step, first_step + count) must already have been simulated
+ * (KMC_E_RANGE otherwise).  Host buffers are caller-owned. */
 int kmc_observables(kmc_handle *h, int64_t first_step, int64_t count, int64_t *J_out,
                     int64_t *zone_counts_out, uint8_t *occ_out_or_null);
+
+/* Per-rail current: J_rail_out[R] receives, for each rail of the device, its
+ * net leftward bond crossings (electrode bonds included) summed over every
+ * step simulated so far; the sum over rails of J_rail_out equals the sum of
+ * kmc_observables' J_out over those steps.  Host buffer of n_rails int64,
+ * caller-owned.  Synchronizes the stream.  Errors: KMC_E_ARG for NULL
+ * arguments, KMC_E_CUDA. */
+int kmc_rail_current(kmc_handle *h, int64_t *J_rail_out);
 
 /* Overwrite V for steps [first_step, first_step + count) from host memory
  * (asynchronous copy on the handle's stream; the host buffer must stay valid
@@ -222,6 +250,8 @@ int kmc_batch_step_n(kmc_batch *b, int64_t n_steps);
 /* kmc_observables for device `inst` of the batch (synchronizes). */
 int kmc_batch_observables(kmc_batch *b, int32_t inst, int64_t first_step, int64_t count,
                           int64_t *J_out, int64_t *zone_counts_out, uint8_t *occ_out_or_null);
+/* kmc_rail_current for device `inst` of the batch (synchronizes). */
+int kmc_batch_rail_current(kmc_batch *b, int32_t inst, int64_t *J_rail_out);
 /* Launch shape: warps per CTA (1, 2, 4, 8) and steps per launch (graph size). */
 int kmc_batch_set_launch(kmc_batch *b, int32_t warps_per_cta, int32_t steps_per_launch);
 /* Autotuner: times every candidate launch shape (warps per CTA in {4, 8},
@@ -264,6 +294,9 @@ void kmc_batch_destroy(kmc_batch *b);
  *   occ_dev          uint8 [n_rails][row_stride] occupancy (0/1 in the first
  *                    n_sites bytes of each row; padding is rewritten as 0),
  *                    16-byte aligned, row_stride a multiple of 16, updated in place;
+ *                    the bytes are not checked (checking would need a
+ *                    synchronisation), and any byte other than 0 or 1 gives
+ *                    undefined results;
  *   N0_dev_or_null   int32 [n_rails] background ion count per rail (the count at
  *                    the device's first step), or NULL to take it from occ_dev
  *                    at this call (right for a device's first call, and for any
@@ -272,8 +305,9 @@ void kmc_batch_destroy(kmc_batch *b);
  *   J_dev            int64 [n_steps] output, as kmc_observables' J_out;
  *   zone_counts_dev  int64 [n_steps][n_zones] output, as zone_counts_out.
  * Only the scalar barrier Ea_eV is used (no per-site table); init_mode, n_ions
- * and fill are ignored; the near-threshold log is not returned.  Results are
- * identical to kmc_step_n on a handle in the same state.
+ * and fill are ignored; rail_base is honoured; the near-threshold log and the
+ * per-rail current are not returned.  Results are identical to kmc_step_n on a
+ * handle in the same state.
  *
  * Working memory is one static device array of about 4 MiB that every GPU
  * loading the library holds until the process exits; it limits n_rails to

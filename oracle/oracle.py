@@ -175,11 +175,22 @@ def zone_field(dev, Nz, N0: int, V: float):
     return dV, B, inv
 
 
+def _shard_rails(dev, rail_ids):
+    """Global rail indices of a device that is a shard (rail_base != 0)."""
+    d = dev if isinstance(dev, dict) else dev.as_dict()
+    base = int(d.get("rail_base", 0))
+    if rail_ids is None and base != 0:
+        return np.arange(base, base + d["R"], dtype=np.int32)
+    return rail_ids
+
+
 def init_occupancy(dev, mode: int, n_ions: int = 0, fill: float = 0.0,
                    rail_ids: Optional[np.ndarray] = None) -> np.ndarray:
     """Initial placement; with rail_ids (Bernoulli only) the rows are those
-    global rails of the device, so P.R must equal len(rail_ids)."""
+    global rails of the device, so P.R must equal len(rail_ids).  A device
+    with rail_base != 0 stands for rails [rail_base, rail_base + R)."""
     P = params(dev)
+    rail_ids = _shard_rails(dev, rail_ids)
     ids = None if rail_ids is None else np.ascontiguousarray(rail_ids, dtype=np.int32)
     if ids is not None:
         P.R = len(ids)
@@ -203,9 +214,10 @@ class OracleSim:
     def __init__(self, dev, V: np.ndarray, occ0: np.ndarray, Ea_site: Optional[np.ndarray] = None,
                  log_cap: int = 4096, nthreads: int = 0, rail_ids: Optional[np.ndarray] = None):
         """rail_ids: global rail index of each row of occ0 (a sample of a larger
-        device); by default row r is rail r."""
+        device); by default row r is rail rail_base + r."""
         self.dev = dev
         self.P = params(dev)
+        rail_ids = _shard_rails(dev, rail_ids)
         self.rail_ids = None if rail_ids is None else np.ascontiguousarray(rail_ids, dtype=np.int32)
         if self.rail_ids is not None:
             self.P.R = len(self.rail_ids)

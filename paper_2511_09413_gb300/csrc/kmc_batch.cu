@@ -287,6 +287,15 @@ int kmc_batch_observables(kmc_batch *b, int32_t inst, int64_t first_step, int64_
     return kmc_observables(b->dev[inst], first_step, count, J_out, zone_counts_out, occ_out_or_null);
 }
 
+int kmc_batch_rail_current(kmc_batch *b, int32_t inst, int64_t *J_rail_out)
+{
+    if (!b) return fail(KMC_E_ARG, "batch is NULL");
+    if (inst < 0 || inst >= (int32_t)b->dev.size()) return fail(KMC_E_ARG, "device index out of range");
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    return kmc_rail_current(b->dev[inst], J_rail_out);
+}
+
 int kmc_batch_set_launch(kmc_batch *b, int32_t warps_per_cta, int32_t steps_per_launch)
 {
     if (!b) return fail(KMC_E_ARG, "batch is NULL");
@@ -306,8 +315,8 @@ int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_
     if (probe_steps < 1) return fail(KMC_E_ARG, "probe_steps must be >= 1");
     if (b->t + probe_steps > b->n_total)
         return fail(KMC_E_RANGE, "probe steps exceed the voltage tables of the batch");
-    // save every device's state (occupancy and counters); the probes advance
-    // real steps from it and it is restored after every probe
+    // save every device's state (occupancy, counters, per-rail current); the
+    // probes advance real steps from it and it is restored after every probe
     cudaError_t e = cudaStreamSynchronize(b->user);
     if (e != cudaSuccess) return cuda_fail(e, "batch sync");
     std::vector<void *> saved(b->dev.size(), nullptr);
@@ -318,24 +327,28 @@ int kmc_batch_tune(kmc_batch *b, int64_t probe_steps, int32_t *warps_out, int32_
     };
     for (size_t i = 0; i < b->dev.size(); ++i) {
         kmc_handle *h = b->dev[i];
-        const size_t bytes = (size_t)h->stride * h->p.n_rails + sizeof(unsigned long long) * 8;
+        const size_t occ_b = (size_t)h->stride * h->p.n_rails;
+        const size_t bytes = occ_b + sizeof(unsigned long long) * 8 + sizeof(int64_t) * h->p.n_rails;
         if ((e = cudaMallocAsync(&saved[i], bytes, b->user)) != cudaSuccess) {
             cleanup();
             return cuda_fail(e, "tune: save buffer");
         }
-        cudaMemcpyAsync(saved[i], h->occ, (size_t)h->stride * h->p.n_rails,
+        cudaMemcpyAsync(saved[i], h->occ, occ_b, cudaMemcpyDeviceToDevice, b->user);
+        cudaMemcpyAsync((char *)saved[i] + occ_b, h->misc, sizeof(unsigned long long) * 8,
                         cudaMemcpyDeviceToDevice, b->user);
-        cudaMemcpyAsync((char *)saved[i] + (size_t)h->stride * h->p.n_rails, h->misc,
-                        sizeof(unsigned long long) * 8, cudaMemcpyDeviceToDevice, b->user);
+        cudaMemcpyAsync((char *)saved[i] + occ_b + sizeof(unsigned long long) * 8, h->Jr,
+                        sizeof(int64_t) * h->p.n_rails, cudaMemcpyDeviceToDevice, b->user);
     }
     auto restore = [&]() {
         cudaStreamSynchronize(b->work);
         for (size_t i = 0; i < b->dev.size(); ++i) {
             kmc_handle *h = b->dev[i];
-            cudaMemcpyAsync(h->occ, saved[i], (size_t)h->stride * h->p.n_rails,
+            const size_t occ_b = (size_t)h->stride * h->p.n_rails;
+            cudaMemcpyAsync(h->occ, saved[i], occ_b, cudaMemcpyDeviceToDevice, b->user);
+            cudaMemcpyAsync(h->misc, (char *)saved[i] + occ_b, sizeof(unsigned long long) * 8,
                             cudaMemcpyDeviceToDevice, b->user);
-            cudaMemcpyAsync(h->misc, (char *)saved[i] + (size_t)h->stride * h->p.n_rails,
-                            sizeof(unsigned long long) * 8, cudaMemcpyDeviceToDevice, b->user);
+            cudaMemcpyAsync(h->Jr, (char *)saved[i] + occ_b + sizeof(unsigned long long) * 8,
+                            sizeof(int64_t) * h->p.n_rails, cudaMemcpyDeviceToDevice, b->user);
             cudaMemsetAsync(h->J + b->t, 0, sizeof(int64_t) * (size_t)probe_steps, b->user);
             cudaMemsetAsync(h->Zc + b->t * h->p.n_zones, 0,
                             sizeof(int64_t) * (size_t)probe_steps * h->p.n_zones, b->user);

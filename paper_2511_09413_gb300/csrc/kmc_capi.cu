@@ -82,6 +82,11 @@ int validate(const kmc_params *p, const double *V, int64_t n_total, const uint8_
     }
     if (p->update_rule != 0 && p->update_rule != 1)
         return fail(KMC_E_ARG, "update_rule must be 0 or 1 (got %d)", p->update_rule);
+    if (p->rail_base < 0 || (int64_t)p->rail_base + p->n_rails > (int64_t)INT32_MAX)
+        return fail(KMC_E_ARG, "rail_base must be >= 0 with rail_base + n_rails <= 2^31 - 1");
+    if (p->rail_base != 0 && p->init_mode == 0)
+        return fail(KMC_E_ARG, "init_mode 0 (exact ion count) is defined over a whole device: "
+                               "it needs rail_base 0 (place a part with init_mode 1 or 2)");
     if (n_total < 0 || n_total >= (int64_t)kInitStep)
         return fail(KMC_E_ARG, "n_steps_total must be in [0, 2^32 - 1)");
     if (n_total > 0 && !V) return fail(KMC_E_ARG, "V_per_step is NULL");
@@ -153,6 +158,7 @@ void fill_args(kmc_handle *h)
     a.Z = p.n_zones;
     a.electrodes = p.electrodes;
     a.instance = p.instance;
+    a.rail_base = (uint32_t)p.rail_base;
     uint32_t k0 = (uint32_t)(p.seed & 0xffffffffu), k1 = (uint32_t)(p.seed >> 32);
     for (int i = 0; i < 10; ++i) {
         a.rk0[i] = k0;
@@ -173,6 +179,7 @@ void fill_args(kmc_handle *h)
     a.log_count = h->misc;
     a.log_cap = h->log_cap;
     a.counters = h->misc + 1;
+    a.Jr = (long long *)h->Jr;
     const int L = p.n_sites, Z = p.n_zones;
     int bnd[KMC_MAX_ZONES + 1];
     for (int z = 0; z <= Z; ++z) bnd[z] = (int)(((int64_t)z * L) / Z);
@@ -271,7 +278,8 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
     h->misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
     h->args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
     h->occ_init = (uint8_t *)h->alloc(occ_bytes);
-    if (!h->occ_init || !h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
+    h->Jr = (int64_t *)h->alloc(sizeof(int64_t) * (size_t)R);
+    if (!h->Jr || !h->occ_init || !h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
         return fail(KMC_E_NOMEM, "device allocation failed");
     if (Ea) {
         h->P0site = (double *)h->alloc(sizeof(double) * (size_t)(R * L));
@@ -286,6 +294,7 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
     CK(cudaMemsetAsync(h->Zc, 0, sizeof(int64_t) * (size_t)std::max<int64_t>(n_total, 1) * (size_t)Z, s),
        "memset");
     CK(cudaMemsetAsync(h->occ, 0, occ_bytes, s), "memset");
+    CK(cudaMemsetAsync(h->Jr, 0, sizeof(int64_t) * (size_t)R, s), "memset");
     CK(setup_constants(p, h->K, s), "constants launch");
     if (n_total > 0)
         CK(cudaMemcpyAsync(h->V, V, sizeof(double) * (size_t)n_total, cudaMemcpyHostToDevice, s),
@@ -439,6 +448,7 @@ int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss
     ga.log_cap = 0;
     ga.log_count = h->g_misc;
     ga.counters = h->g_misc + 1;
+    ga.Jr = nullptr;
     ga.wJ = dLoss_dJ ? h->g_wJ : nullptr;
     ga.fJab = dLoss_dJ ? (const double2 *)h->g_fJab : nullptr;
     ga.fZa = dLoss_dZc ? h->g_fZa : nullptr;
@@ -569,6 +579,16 @@ int kmc_observables(kmc_handle *h, int64_t first_step, int64_t count, int64_t *J
                              (size_t)h->p.n_sites, (size_t)h->p.n_rails, cudaMemcpyDeviceToHost, s),
            "copy occupancy");
     CK(cudaStreamSynchronize(s), "observables");
+    return KMC_OK;
+}
+
+int kmc_rail_current(kmc_handle *h, int64_t *J_rail_out)
+{
+    if (!h || !J_rail_out) return fail(KMC_E_ARG, "handle or J_rail_out is NULL");
+    CK(cudaMemcpyAsync(J_rail_out, h->Jr, sizeof(int64_t) * (size_t)h->p.n_rails,
+                       cudaMemcpyDeviceToHost, h->stream),
+       "copy per-rail current");
+    CK(cudaStreamSynchronize(h->stream), "rail current");
     return KMC_OK;
 }
 

@@ -44,6 +44,7 @@ struct kmc_handle {
     kmc::SweepArgs *args_dev = nullptr;       // device copy of args for the kernels' rare paths
     int64_t log_cap = 4096;
     uint8_t *occ_init = nullptr;              // occupancy at step 0: the gradient pass's checkpoint
+    int64_t *Jr = nullptr;                    // [R] per-rail net leftward crossings so far
 
     // gradient pass (allocated at the first kmc_grad)
     uint8_t *g_occ = nullptr;                 // replayed occupancy

@@ -36,6 +36,7 @@ struct SweepArgs {
     int64_t stride;            // bytes per rail (L rounded up to 16)
     int32_t R, L, Z, electrodes;
     uint32_t instance;
+    uint32_t rail_base;        // global index of local rail 0 (Philox counter word 1, log)
     uint32_t rk0[10], rk1[10]; // Philox round keys (seed words plus Weyl increments)
     int64_t t0;                // absolute step of the first step of this launch
     int32_t n_steps;
@@ -53,6 +54,7 @@ struct SweepArgs {
     unsigned long long *log_count;
     int64_t log_cap;
     unsigned long long *counters; // [3] philox blocks, exact decisions, moves
+    long long *Jr;                // [R] per-rail net leftward crossings, accumulated, or null
     int32_t bnd[kMaxZones + 1];   // zone boundaries floor(z L / Z)
     int32_t wsum[kMaxZones + 1];  // w_{z-1} + w_z (w_{-1} = w_Z = 0)
     float cz[kMaxZones];          // ((b_z + b_{z+1}) - H / L) / (2 L), H = sum w_z (b_z + b_{z+1})

@@ -79,6 +79,14 @@ int scratch_for_current_device(unsigned char **out)
 
 bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
+// Writes the launch arguments into the scratch array from the kernel's own
+// parameter space, so that no host buffer has to outlive the call (a copy
+// from host memory would read the caller's stack frame when it executes).
+__global__ void store_args_kernel(const SweepArgs a, SweepArgs *dst)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = a;
+}
+
 }  // namespace
 
 extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t row_stride,
@@ -96,6 +104,8 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
         return fail(KMC_E_ARG, "n_zones must be in [1, min(n_sites, 32)]");
     if (p->electrodes != 0 && p->electrodes != 1) return fail(KMC_E_ARG, "electrodes must be 0 or 1");
     if (p->update_rule != 0 && p->update_rule != 1) return fail(KMC_E_ARG, "update_rule must be 0 or 1");
+    if (p->rail_base < 0 || (int64_t)p->rail_base + p->n_rails > (int64_t)INT32_MAX)
+        return fail(KMC_E_ARG, "rail_base must be >= 0 with rail_base + n_rails <= 2^31 - 1");
     if (!finite_pos(p->site_spacing_nm) || !finite_pos(p->dt_s) || !finite_pos(p->T_K))
         return fail(KMC_E_ARG, "site_spacing_nm, dt_s and T_K must be > 0");
     if (!(isfinite(p->nu_Hz) && p->nu_Hz >= 0.0) || !isfinite(p->Ea_eV) || !isfinite(p->alpha_V) ||
@@ -160,6 +170,7 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     a.Z = Z;
     a.electrodes = p->electrodes;
     a.instance = p->instance;
+    a.rail_base = (uint32_t)p->rail_base;
     uint32_t k0 = (uint32_t)(p->seed & 0xffffffffu), k1 = (uint32_t)(p->seed >> 32);
     for (int i = 0; i < 10; ++i) {
         a.rk0[i] = k0;
@@ -181,6 +192,7 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     a.log_count = misc;
     a.log_cap = kLogCap;
     a.counters = misc + 1;
+    a.Jr = nullptr;     // no per-rail current on this path
     int bnd[KMC_MAX_ZONES + 1];
     for (int z = 0; z <= Z; ++z) bnd[z] = (int)(((int64_t)z * L) / Z);
     for (int z = 0; z <= KMC_MAX_ZONES; ++z) a.bnd[z] = z <= Z ? bnd[z] : L;
@@ -226,9 +238,8 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     l.grid = (int)((R + rails_per_cta - 1) / rails_per_cta);
     a.flush = flush;
 
-    if ((e = cudaMemcpyAsync(args_dev, &a, sizeof(SweepArgs), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
-        return cuda_fail(e, "copy arguments");
+    store_args_kernel<<<1, 32, 0, s>>>(a, args_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "argument store launch");
     int64_t left = n_steps;
     while (left > 0) {
         const int64_t n = std::min<int64_t>(left, 1 << 30);

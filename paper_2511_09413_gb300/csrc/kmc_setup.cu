@@ -37,8 +37,9 @@ __device__ __forceinline__ uint4 philox_init(uint32_t site, uint32_t rail, uint3
 
 __device__ __forceinline__ uint64_t init_key(const kmc_params &p, int64_t idx)
 {
-    const uint32_t rail = (uint32_t)(idx / p.n_sites);
-    const uint32_t site = (uint32_t)(idx - (int64_t)rail * p.n_sites);
+    const int64_t row = idx / p.n_sites;                       // the rail's row in this device
+    const uint32_t site = (uint32_t)(idx - row * p.n_sites);
+    const uint32_t rail = (uint32_t)p.rail_base + (uint32_t)row;  // its global index
     const uint4 x = philox_init(site, rail, p.instance, (uint32_t)(p.seed & 0xffffffffu),
                                 (uint32_t)(p.seed >> 32));
     return ((uint64_t)x.y << 32) | x.x;

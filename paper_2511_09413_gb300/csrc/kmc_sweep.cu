@@ -121,7 +121,8 @@ struct Layout {
     static constexpr size_t INJ = OW + align16(4 * W);         // int [2][G]
     static constexpr size_t N0S = INJ + align16(4 * 2 * G);    // int [G]
     static constexpr size_t FS = N0S + align16(4 * G);         // int [G]
-    static constexpr size_t NDEF = FS + align16(4 * G);        // int [4]
+    static constexpr size_t JR = FS + align16(4 * G);          // int [G]: per-rail current
+    static constexpr size_t NDEF = JR + align16(4 * G);        // int [4]
     static constexpr size_t DEF = NDEF + 16;                   // uint16 [kDeferCap]
     static constexpr size_t LST = DEF + align16(2 * 64);       // uint16 [LIST]
     static constexpr size_t FIXED = LST + align16(2 * LIST);
@@ -173,6 +174,8 @@ struct WarpSmem {
     __device__ int32_t *inj() const { return (int32_t *)(b + Ly::INJ); }
     __device__ int32_t *N0s() const { return (int32_t *)(b + Ly::N0S); }
     __device__ int32_t *Fs() const { return (int32_t *)(b + Ly::FS); }
+    // net leftward crossings of each rail of the warp since the last flush
+    __device__ int32_t *jr() const { return (int32_t *)(b + Ly::JR); }
     __device__ int32_t *ndef() const { return (int32_t *)(b + Ly::NDEF); }
     // window mid voltage (FP32), stored next to the deferral counter
     __device__ float &vmid_ref() const { return *(float *)(b + Ly::NDEF + 4); }
@@ -357,14 +360,15 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
 {
     const uint16_t dsc = S.list()[i];
     const int site = dsc & 0x7FF, g2 = LPR == 32 ? 0 : dsc >> 11;
-    const uint32_t r2 = (uint32_t)(rail0 + g2);
+    const int64_t r2 = rail0 + g2;                      // the rail's row in this device
+    const uint32_t rg = g->rail_base + (uint32_t)r2;    // its global index (Philox, log)
     // the bounded decision needs only the high words (x1, x3) of the draw; the
     // exact pass recomputes the whole block
-    const uint4 x = exact ? philox((uint32_t)site, r2, t, g->instance, g->rk0, g->rk1)
+    const uint4 x = exact ? philox((uint32_t)site, rg, t, g->instance, g->rk0, g->rk1)
                           : make_uint4(0u, xy, 0u, xw);
     const int z = zone_tab[site];
     const bool isE = i >= n_inner;
-    Decision D = decide<LPR, WPL>(S, g, x, site, g2, z, isE, persite, flo, fhi, (int64_t)r2);
+    Decision D = decide<LPR, WPL>(S, g, x, site, g2, z, isE, persite, flo, fhi, r2);
     const bool undecided = D.dR == 2 || D.dL == 2;
     if (!exact) {
         if (undecided) {
@@ -379,20 +383,20 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
     const int L = g->L, Z = g->Z;
     double B, inv;
     exact_zone(S.Pb() + g2 * (Z + 1), K, Z, L, S.N0s()[g2], g->V[t], z, &B, &inv);
-    const double P0k = persite ? g->P0site[(int64_t)r2 * L + site] : K->P0;
+    const double P0k = persite ? g->P0site[r2 * L + site] : K->P0;
     unsigned ne = 0;
     if (D.dR == 2) {
         const double base = D.kindR == 1 ? K->E_in : (D.kindR == 2 ? K->E_out : P0k);
         const double p = __dmul_rn(__dmul_rn(base, inv), B);       // Eq. 6
         D.dR = exact_trial(((uint64_t)x.y << 32) | x.x, p, g->log, g->log_count, g->log_cap,
-                           (int32_t)r2, t, site, 0, D.kindR) ? 1 : 0;
+                           (int32_t)rg, t, site, 0, D.kindR) ? 1 : 0;
         ++ne;
     }
     if (D.dL == 2) {
         const double base = D.kindL == 1 ? K->E_in : (D.kindL == 2 ? K->E_out : P0k);
         const double p = __dmul_rn(base, inv);                      // Eq. 5
         D.dL = exact_trial(((uint64_t)x.w << 32) | x.z, p, g->log, g->log_count, g->log_cap,
-                           (int32_t)r2, t, site, 1, D.kindL) ? 1 : 0;
+                           (int32_t)rg, t, site, 1, D.kindL) ? 1 : 0;
         ++ne;
     }
     atomicAdd(&g->counters[1], (unsigned long long)ne);
@@ -600,6 +604,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     const bool persite = a.P0bnd != nullptr;
     const int64_t rail0 = tile_rail0 + (int64_t)warp * G;
     const int64_t rail = rail0 + seg;
+    // Philox counter word 1 of the warp's first rail: the global rail index
+    const uint32_t prail0 = a.rail_base + (uint32_t)rail0;
     const bool active = rail < a.R;
     const int nact = (int)max((int64_t)0, min((int64_t)G, (int64_t)a.R - rail0));
 
@@ -667,6 +673,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     }
     for (int i = lane; i < 2 * G; i += 32) S.inj()[i] = 0;
     if (sl == 0) S.N0s()[seg] = active ? a.N0[rail] : 0;
+    if (sl == 0) S.jr()[seg] = 0;
     if (persite) {
         for (int pi = lane; pi < G * Z; pi += 32) {
             const int64_t r2 = rail0 + pi / Z;
@@ -970,7 +977,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         const bool has = i < nlist;
                         const uint16_t d = S.list()[has ? i : i0];
                         const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
-                        const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
+                        const uint4 x = philox((uint32_t)site, prail0 + (uint32_t)g, t, instance,
                                                rk0, rk1);
                         const int ts = i >= n_inner ? G * Z + (i - n_inner)
                                                     : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]);
@@ -1031,7 +1038,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         // instance words are then warp-uniform and the compiler hoists
                         // the parts of the first two Philox rounds that depend only on them
                         const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
-                        const uint4 x = philox((uint32_t)site, (uint32_t)(rail0 + g), t, instance,
+                        const uint4 x = philox((uint32_t)site, prail0 + (uint32_t)g, t, instance,
                                                rk0, rk1);
                         // electrode sites have their own entries after the G Z zone entries
                         const int ts = i >= n_inner ? G * Z + (i - n_inner)
@@ -1168,6 +1175,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 } else {
                     const int Jw = __reduce_add_sync(FULL, Jl);
                     if (lane == 0 && Jw != 0) atomicAdd(&tr[0], Jw);
+                    // per-rail current: the rail's own sum (the warp's when G == 1)
+                    if (a.Jr) {
+                        if (G == 1) {
+                            if (lane == 0 && Jw != 0) S.jr()[0] += Jw;
+                        } else {
+                            int v = Jl;
+#pragma unroll
+                            for (int off2 = LPR / 2; off2 >= 1; off2 >>= 1)
+                                v += __shfl_xor_sync(FULL, v, off2, LPR);
+                            if (sl == 0 && v != 0) S.jr()[seg] += v;
+                        }
+                    }
                 }
             }
             if constexpr (GRAD) {
@@ -1207,6 +1226,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         if (lane == 0) {
             if (n_draw) atomicAdd(&a.counters[0], (unsigned long long)n_draw);
             if (m) atomicAdd(&a.counters[2], (unsigned long long)m);
+        }
+        // the rail's current of this chunk (at most (L + 1) flush per rail: no
+        // int32 overflow) into its int64 total; each rail belongs to one warp
+        if (a.Jr && active && sl == 0) {
+            const int v = S.jr()[seg];
+            if (v != 0) a.Jr[rail] += v;
+            S.jr()[seg] = 0;
         }
         n_draw = n_move = 0;
         __syncthreads();

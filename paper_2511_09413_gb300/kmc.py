@@ -47,7 +47,7 @@ class kmc_params(ctypes.Structure):
         ("rho_electrode", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32), ("init_mode", ctypes.c_int32),
         ("n_ions", ctypes.c_int64), ("fill", ctypes.c_double),
-        ("update_rule", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("update_rule", ctypes.c_int32), ("rail_base", ctypes.c_int32),
     ]
 
 
@@ -73,7 +73,8 @@ EXPORTS = ["kmc_set_allocator", "kmc_create", "kmc_step_n", "kmc_observables", "
            "kmc_batch_step_n", "kmc_batch_observables", "kmc_batch_set_launch", "kmc_batch_tune",
            "kmc_batch_current_step", "kmc_batch_destroy", "kmc_set_accept_path",
            "kmc_accept_path", "kmc_batch_set_accept_path", "kmc_batch_accept_path", "kmc_grad",
-           "kmc_batch_grad", "kmc_philox_probe", "kmc_batch_grad_all"]
+           "kmc_batch_grad", "kmc_philox_probe", "kmc_batch_grad_all", "kmc_rail_current",
+           "kmc_batch_rail_current"]
 
 _lib = None
 
@@ -96,6 +97,10 @@ def load(path: str = LIB_PATH):
     L.kmc_observables.argtypes = [vp, i64, i64, P(ctypes.c_int64), P(ctypes.c_int64),
                                   P(ctypes.c_uint8)]
     L.kmc_set_voltage.argtypes = [vp, i64, i64, P(ctypes.c_double)]
+    L.kmc_rail_current.argtypes = [vp, P(ctypes.c_int64)]
+    L.kmc_rail_current.restype = ctypes.c_int
+    L.kmc_batch_rail_current.argtypes = [vp, ctypes.c_int32, P(ctypes.c_int64)]
+    L.kmc_batch_rail_current.restype = ctypes.c_int
     L.kmc_near_threshold_log.argtypes = [vp, P(kmc_log_entry), i64, P(ctypes.c_int64)]
     L.kmc_counters.argtypes = [vp, P(ctypes.c_uint64)]
     L.kmc_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -186,19 +191,28 @@ def kmc_observables(h: int, first_step: int, count: int, J_out: Optional[np.ndar
                                   _ptr(occ_out, ctypes.c_uint8)))
 
 
+def kmc_rail_current(h: int, n_rails: int) -> np.ndarray:
+    out = np.zeros(n_rails, dtype=np.int64)
+    _check(load().kmc_rail_current(ctypes.c_void_p(h), _ptr(out, ctypes.c_int64)))
+    return out
+
+
 def kmc_set_voltage(h: int, first_step: int, V_host: np.ndarray):
     V = np.ascontiguousarray(V_host, dtype=np.float64)
     _check(load().kmc_set_voltage(ctypes.c_void_p(h), int(first_step), V.shape[0],
                                   _ptr(V, ctypes.c_double)))
 
 
-def kmc_near_threshold_log(h: int, cap: int = 4096) -> np.ndarray:
+def kmc_near_threshold_log(h: int, cap: int = 4096, with_total: bool = False):
+    """Logged near-threshold decisions (at most cap); with_total also returns
+    how many were logged in all (more than returned if the log overflowed)."""
     buf = np.zeros(cap, dtype=LOG_DTYPE)
     n = ctypes.c_int64()
     _check(load().kmc_near_threshold_log(ctypes.c_void_p(h),
                                          buf.ctypes.data_as(ctypes.POINTER(kmc_log_entry)), cap,
                                          ctypes.byref(n)))
-    return buf[:min(n.value, cap)].copy()
+    out = buf[:min(n.value, cap)].copy()
+    return (out, int(n.value)) if with_total else out
 
 
 def kmc_counters(h: int) -> np.ndarray:
@@ -272,7 +286,7 @@ def params_from_device(dev, init_mode: int, n_ions: int = 0, fill: float = 0.0) 
                       k_electrode_Hz=d["k_e"], rho_electrode=d["rho_e"],
                       seed=d["seed"] & 0xFFFFFFFFFFFFFFFF, instance=d["instance"],
                       init_mode=init_mode, n_ions=n_ions, fill=fill,
-                      update_rule=d.get("rule", 0), reserved=0)
+                      update_rule=d.get("rule", 0), rail_base=d.get("rail_base", 0))
 
 
 _torch_alloc_cb = None
@@ -330,13 +344,17 @@ class Sim:
         kmc_observables(self.h, 0, 0, None, None, occ)
         return occ
 
+    def rail_current(self) -> np.ndarray:
+        """Net leftward crossings of each rail over every step so far (kmc_rail_current)."""
+        return kmc_rail_current(self.h, self.R)
+
     def grad(self, dLoss_dJ: Optional[np.ndarray] = None, dLoss_dZc: Optional[np.ndarray] = None):
         """Likelihood-ratio gradient of E[F] (kmc_grad): (grad[4], stderr[4])
         with respect to (Ea, nu, kappa, fill)."""
         return kmc_grad(self.h, self.t, self.Z, dLoss_dJ, dLoss_dZc)
 
-    def near_threshold_log(self, cap: int = 4096) -> np.ndarray:
-        return kmc_near_threshold_log(self.h, cap)
+    def near_threshold_log(self, cap: int = 4096, with_total: bool = False):
+        return kmc_near_threshold_log(self.h, cap, with_total)
 
     def counters(self) -> np.ndarray:
         return kmc_counters(self.h)
@@ -394,6 +412,12 @@ def kmc_batch_observables(b: int, inst: int, first_step: int, count: int,
                                         _ptr(J_out, ctypes.c_int64),
                                         _ptr(zone_counts_out, ctypes.c_int64),
                                         _ptr(occ_out, ctypes.c_uint8)))
+
+
+def kmc_batch_rail_current(b: int, inst: int, n_rails: int) -> np.ndarray:
+    out = np.zeros(n_rails, dtype=np.int64)
+    _check(load().kmc_batch_rail_current(ctypes.c_void_p(b), int(inst), _ptr(out, ctypes.c_int64)))
+    return out
 
 
 def kmc_batch_set_launch(b: int, warps_per_cta: int, steps_per_launch: int):
@@ -536,6 +560,9 @@ class Batch:
         occ = np.zeros((R, L), dtype=np.uint8)
         kmc_batch_observables(self.h, inst, 0, 0, None, None, occ)
         return occ
+
+    def rail_current(self, inst: int) -> np.ndarray:
+        return kmc_batch_rail_current(self.h, inst, self.shapes[inst][0])
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,13 +1,16 @@
 """Host-side logic of running the sweep on several GPUs, one process per GPU.
 
-Rails, and whole device instances, are independent: a rank advances its own
-instances with no exchange on the data path.  Each rank owns the instances
-i with i % world == rank (the instance is Philox counter word 3, so every
-instance draws its own stream).  The only collectives are the readout (the
-int64 sums of the ranks' current and zone-count traces, when a single
-ensemble trace is wanted) and the timing (the maximum over ranks, which the
-whole-job throughput divides by).  Works with any torch.distributed backend:
-gloo with CPU tensors, NCCL with CUDA tensors.
+Rails are independent (the zone field of a rail depends on that rail alone),
+so a device is partitioned by rails: rank k advances the contiguous rows
+[r0, r1) of shard_rails() as a device of r1 - r0 rails with rail_base = r0.
+The rail index is Philox counter word 1 and the placement key, so the rank
+reproduces exactly those rows of the whole device, with no exchange on the
+data path.  Whole device instances can be dealt out too (shard_instances:
+instance i to rank i % world; the instance is counter word 3).  The only
+collectives are the readout (the int64 sums of the ranks' current and
+zone-count traces, when one device-wide trace is wanted) and the timing (the
+maximum over ranks, which the whole-job throughput divides by).  Works with
+any torch.distributed backend: gloo with CPU tensors, NCCL with CUDA tensors.
 """
 from __future__ import annotations
 
@@ -21,6 +24,16 @@ def rank_info():
     import os
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def shard_rails(n_rails: int, rank: int, world: int):
+    """(r0, r1): the contiguous rails of a device this rank advances.  The
+    first n_rails % world ranks take one rail more than the others."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    q, m = divmod(int(n_rails), world)
+    r0 = rank * q + min(rank, m)
+    return r0, r0 + q + (1 if rank < m else 0)
 
 
 def shard_instances(n_instances: int, rank: int, world: int) -> List[int]:

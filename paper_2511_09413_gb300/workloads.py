@@ -46,6 +46,8 @@ class Device:
     seed: int = 0
     instance: int = 0
     rule: int = 0          # 0 synchronous update, 1 brick-wall (even/odd bonds)
+    rail_base: int = 0     # global index of rail 0: this device is rows
+                           # [rail_base, rail_base + R) of a larger one (a shard)
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)
@@ -115,14 +117,20 @@ def random_occupancy(R: int, L: int, fill: float, seed: int) -> np.ndarray:
     return (rng.random((R, L)) < fill).astype(np.uint8)
 
 
-def normal_barriers(R: int, L: int, mean: float, sigma: float, seed: int) -> np.ndarray:
-    """Per-site migration barriers Ea ~ N(mean, sigma) in eV."""
-    rng = np.random.default_rng(seed)
+def normal_barriers(R: int, L: int, mean: float, sigma: float, seed: int,
+                    row0: int = 0) -> np.ndarray:
+    """Per-site migration barriers Ea ~ N(mean, sigma) in eV: rows
+    [row0, row0 + R) of a device's table.  The table is drawn in blocks of
+    B = max(1, 2^22 // L) rows, block b from its own PCG64 stream seeded with
+    (seed, b), so that any range of rows (the shard of one rank) is generated
+    alone and equals those rows of the whole table."""
     out = np.empty((R, L), dtype=np.float64)
-    rows = max(1, (1 << 22) // max(L, 1))
-    for r0 in range(0, R, rows):
-        r1 = min(R, r0 + rows)
-        out[r0:r1] = rng.normal(mean, sigma, size=(r1 - r0, L))
+    B = max(1, (1 << 22) // max(L, 1))
+    g0, g1 = row0, row0 + R
+    for b in range(g0 // B, (g1 - 1) // B + 1 if R > 0 else 0):
+        blk = np.random.default_rng([seed, b]).normal(mean, sigma, size=(B, L))
+        lo, hi = max(g0, b * B), min(g1, (b + 1) * B)
+        out[lo - g0:hi - g0] = blk[lo - b * B:hi - b * B]
     return out
 
 
@@ -139,13 +147,17 @@ def relaxation_64x100(n_polarise: int = 5000, n_total: int = 10000) -> Workload:
 
 
 def hysteresis_65536x1024(R: int = 65536, L: int = 1024, steps_per_cycle: int = 100000,
-                          cycles: int = 2, seed: int = 1, with_barriers: bool = True) -> Workload:
+                          cycles: int = 2, seed: int = 1, with_barriers: bool = True,
+                          rail_base: int = 0) -> Workload:
     """Plain large device: 65,536 rails x 1,024 sites, 25 % filling,
     Ea per site ~ N(0.40, 0.02) eV, T = 300 K, triangular sweep +-2 V at
     1e5 steps per cycle for 2 cycles, injecting/extracting electrodes with
-    rate 1e9 Hz (reservoir density = the initial filling)."""
-    dev = Device(R=R, L=L, Z=10, electrodes=1, k_e=1e9, rho_e=0.25, seed=seed)
-    Ea = normal_barriers(R, L, 0.40, 0.02, seed + 1000) if with_barriers else None
+    rate 1e9 Hz (reservoir density = the initial filling).  With rail_base,
+    rails [rail_base, rail_base + R) of a larger device of the same recipe."""
+    dev = Device(R=R, L=L, Z=10, electrodes=1, k_e=1e9, rho_e=0.25, seed=seed,
+                 rail_base=rail_base)
+    Ea = (normal_barriers(R, L, 0.40, 0.02, seed + 1000, row0=rail_base)
+          if with_barriers else None)
     return Workload("hysteresis_%dx%d" % (R, L), dev,
                     triangle_protocol(2.0, steps_per_cycle, cycles),
                     init_mode=1, fill=0.25, Ea_site=Ea)

@@ -48,6 +48,7 @@ def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(kmc.kmc_params) == 4 * 4 + 9 * 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4
     assert kmc.kmc_params.seed.offset == 16 + 72
     assert kmc.kmc_params.update_rule.offset == 16 + 72 + 8 + 4 + 4 + 8 + 8
+    assert kmc.kmc_params.rail_base.offset == kmc.kmc_params.update_rule.offset + 4
     assert ctypes.sizeof(kmc.kmc_log_entry) == 32
     assert kmc.LOG_DTYPE.itemsize == 32
 
@@ -67,7 +68,8 @@ def _params(**kw):
     dict(site_spacing_nm=float("nan")), dict(nu_Hz=-1.0), dict(init_mode=3),
     dict(init_mode=1, fill=1.5), dict(init_mode=0, n_ions=401), dict(init_mode=2),
     dict(electrodes=1, rho_electrode=1.5), dict(kappa=float("inf")), dict(update_rule=2),
-    dict(update_rule=-1),
+    dict(update_rule=-1), dict(rail_base=-1), dict(rail_base=2 ** 31 - 3),
+    dict(init_mode=0, n_ions=10, rail_base=8),
 ])
 def test_validation_rejects_bad_parameters_on_host(lib, bad):
     from paper_2511_09413_gb300 import kmc
@@ -96,6 +98,8 @@ def test_null_handle_calls_fail_cleanly(lib):
     from paper_2511_09413_gb300 import kmc
     assert lib.kmc_step_n(None, 1) == kmc.KMC_E_ARG
     assert lib.kmc_observables(None, 0, 0, None, None, None) == kmc.KMC_E_ARG
+    assert lib.kmc_rail_current(None, None) == kmc.KMC_E_ARG
+    assert lib.kmc_batch_rail_current(None, 0, None) == kmc.KMC_E_ARG
     assert lib.kmc_current_step(None) == -1
     lib.kmc_destroy(None)
     g = (ctypes.c_double * 4)()
@@ -138,5 +142,5 @@ def test_device_maps_to_the_same_quantities_on_both_sides():
     for a, b in pairs:
         assert getattr(p, a) == getattr(q, b), (a, b)
         assert getattr(q, b) == {"seed": (-5) & 0xFFFFFFFFFFFFFFFF}.get(b, dev.as_dict()[b])
-    assert p.init_mode == 1 and p.fill == 0.3 and p.reserved == 0
+    assert p.init_mode == 1 and p.fill == 0.3 and p.rail_base == 0
     assert kmc.params_from_device(dev.as_dict(), init_mode=0, n_ions=9).n_ions == 9

@@ -40,7 +40,7 @@ def _traffic_fixture(tmp_path, source: bytes, recorded_sha: str):
     (tmp_path / "profiles").mkdir()
     (tmp_path / "k.cu").write_bytes(source)
     rec = {"kernel_source": "k.cu", "kernel_source_sha256": recorded_sha, "rails": 16384,
-           "dram_bytes_read": 1000, "dram_bytes_write": 24}
+           "steps_per_launch": 10000, "dram_bytes_read": 1000, "dram_bytes_write": 24}
     (tmp_path / "profiles" / "sweep_traffic.json").write_text(json.dumps(rec))
 
 
@@ -48,16 +48,18 @@ def test_traffic_scaled_by_rails_while_the_source_matches(tmp_path, monkeypatch)
     src = b"__global__ void k() {}\n"
     _traffic_fixture(tmp_path, src, hashlib.sha256(src).hexdigest())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic_per_launch(16384) == 1024
-    assert bench._traffic_per_launch(65536) == 4096
+    assert bench._traffic_per_launch(16384, 10000) == 1024
+    assert bench._traffic_per_launch(65536, 10000) == 4096
+    # a capture of launches of another length says nothing about this one
+    assert bench._traffic_per_launch(65536, 1000) is None
 
 
 def test_traffic_withdrawn_when_the_source_changed(tmp_path, monkeypatch):
     _traffic_fixture(tmp_path, b"changed\n", hashlib.sha256(b"original\n").hexdigest())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic_per_launch(65536) is None
+    assert bench._traffic_per_launch(65536, 10000) is None
     monkeypatch.setattr(bench, "ROOT", str(tmp_path / "missing"))
-    assert bench._traffic_per_launch(65536) is None
+    assert bench._traffic_per_launch(65536, 10000) is None
 
 
 def test_committed_traffic_record_names_the_sweep_kernel_source():
@@ -65,6 +67,7 @@ def test_committed_traffic_record_names_the_sweep_kernel_source():
         rec = json.load(f)
     assert rec["kernel_source"] == "paper_2511_09413_gb300/csrc/kmc_sweep.cu"
     assert rec["rails"] > 0 and rec["dram_bytes_read"] > 0 and rec["dram_bytes_write"] >= 0
+    assert rec["steps_per_launch"] > 0
     assert "--clock-control none" in rec["command"]
 
 
@@ -103,3 +106,12 @@ def test_clock_samples_parsed(lines, median, reasons):
 def test_clock_sampler_without_nvidia_smi():
     s = bench.ClockSampler(0)
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_alu_peak_is_derived_from_unit_counts_and_clock():
+    """The roofline's integer-pipe peak: 152 SMs x 64 IMAD lanes per clock at
+    the maximum SM clock over 34 IMAD issue slots per Philox4x32-10 block
+    (16 widening multiplies at two slots, two low halves at one)."""
+    assert bench.PHILOX_IMAD_SLOTS == 16 * 2 + 2
+    peak = bench.SMS * bench.IMAD_PER_SM_PER_CLK * 2070e6 / bench.PHILOX_IMAD_SLOTS
+    assert abs(peak - 5.922e11) < 1e8

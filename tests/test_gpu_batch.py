@@ -34,7 +34,7 @@ def _batch_case(n, n_steps, seed=0):
                          T=300.0, Ea=float(rng.uniform(0.38, 0.42)), nu=1e12,
                          alpha=float(rng.uniform(0.0, 0.5)), kappa=1.0, k_e=2e6 if el else 0.0,
                          rho_e=float(rng.uniform(0.1, 0.6)) if el else 0.0, seed=77,
-                         instance=1000 + i))
+                         instance=1000 + i, rail_base=int(rng.choice([0, 0, 5000]))))
         # each device its own protocol: a triangle of random amplitude and period
         period = int(rng.integers(50, 400))
         Vs.append(W.triangle_protocol(float(rng.uniform(0.5, 4.0)), period,
@@ -51,6 +51,7 @@ def _check_against_oracle(b, devs, Vs, occs, n_steps):
         assert np.array_equal(Zg, Zo), i
         assert np.array_equal(Jg, Jo), i
         assert np.array_equal(b.occupancy(i), orc.occ), i
+        assert np.array_equal(b.rail_current(i), orc.J_rail), i
 
 
 def test_batch_bit_exact_with_graph_replays(kmc):

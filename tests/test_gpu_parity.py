@@ -1,12 +1,16 @@
 """GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle on the
-same seeded inputs.  Occupancy trajectories, per-step current and zone counts
-must be bit-identical; integer traces leave no room for tolerance.  Near-
-threshold decisions (|u - p| < 1e-12) must be logged identically."""
+same seeded inputs.  Occupancy trajectories, per-step current, per-rail
+current and zone counts must be bit-identical; integer traces leave no room
+for tolerance.  Near-threshold decisions (|u - p| < 1e-12, S2.1.7's "u <= p")
+must be logged identically: the same (rail, step, site, direction, kind) set,
+and u - p equal to 1e-15 (both sides compute it in FP64 from the same u and a
+p that can differ by an ulp of exp)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2511_09413_gb300 import workloads as W
+from tests.near_threshold import forced_device
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +34,25 @@ def _dev(**kw):
     return d
 
 
+LOG_KEYS = ("rail", "step", "site", "dir", "kind")
+
+
+def _sorted_log(log):
+    order = np.lexsort(tuple(log[k] for k in reversed(LOG_KEYS)))
+    return log[order]
+
+
+def assert_logs_equal(lg, lo):
+    """Near-threshold logs: equal as sets of (rail, step, site, dir, kind), with
+    u - p equal to 1e-15 (the logs are filled in a nondeterministic order)."""
+    assert len(lg) == len(lo), (len(lg), len(lo))
+    a, b = _sorted_log(lg), _sorted_log(lo)
+    for k in LOG_KEYS:
+        assert np.array_equal(a[k], b[k]), k
+    assert np.all(np.abs(a["diff"] - b["diff"]) <= 1e-15)
+    assert np.all(np.abs(a["diff"]) < 1e-12)
+
+
 def _compare(kmc, dev, V, occ0, Ea=None, chunks=None, warps=0, flush=0, accept=-1):
     """Run GPU and oracle from the same occupancy; compare everything."""
     n = len(V)
@@ -48,11 +71,15 @@ def _compare(kmc, dev, V, occ0, Ea=None, chunks=None, warps=0, flush=0, accept=-
     assert np.array_equal(Zg, Zo), "zone-count traces differ"
     assert np.array_equal(Jg, Jo), "current traces differ"
     assert np.array_equal(occ_g, orc.occ), "final occupancy differs"
-    lg, lo = sim.near_threshold_log(), orc.near_threshold_log()
-    assert len(lg) == len(lo)
+    Jr = sim.rail_current()
+    assert np.array_equal(Jr, orc.J_rail), "per-rail current differs"
+    assert Jr.sum() == Jg.sum()
+    lg, n_lg = sim.near_threshold_log(with_total=True)
+    assert n_lg == len(lg) and int(orc.log_count[0]) == n_lg, "log overflowed or counts differ"
+    assert_logs_equal(lg, orc.near_threshold_log())
     cnt = sim.counters()
     sim.close()
-    return Jg, Zg, occ_g, cnt
+    return Jg, Zg, occ_g, cnt, lg
 
 
 def test_relaxation_64x100_full_run_bit_exact(kmc):
@@ -69,7 +96,8 @@ def test_relaxation_64x100_full_run_bit_exact(kmc):
     assert np.array_equal(Zg, Zo)
     assert np.array_equal(Jg, Jo)
     assert np.array_equal(sim.occupancy(), orc.occ)
-    assert len(sim.near_threshold_log()) == len(orc.near_threshold_log())
+    assert np.array_equal(sim.rail_current(), orc.J_rail)
+    assert_logs_equal(sim.near_threshold_log(), orc.near_threshold_log())
     sim.close()
 
 
@@ -133,7 +161,7 @@ def test_strong_space_charge_and_large_bias(kmc):
     dev = _dev(R=16, L=200, Z=10, alpha=3.0, kappa=1.0, electrodes=1, k_e=1e7, rho_e=0.9)
     occ0 = W.random_occupancy(16, 200, 0.6, seed=3)
     V = np.concatenate([np.full(200, 60.0), np.full(200, -60.0), np.zeros(100)])
-    _, _, _, cnt = _compare(kmc, dev, V, occ0)
+    _, _, _, cnt, _ = _compare(kmc, dev, V, occ0)
     assert cnt[1] > 0   # some decisions needed the exact path
 
 
@@ -198,6 +226,59 @@ def test_near_threshold_decision_logged(kmc):
     sim.close()
 
 
+@pytest.mark.parametrize("accept", [0, 1])
+@pytest.mark.parametrize("R,L,electrodes", [(12, 100, 0), (9, 37, 1), (5, 1024, 1),
+                                            (3, 2048, 0), (20, 300, 1)])
+def test_forced_near_threshold_decisions_logged_identically(kmc, R, L, electrodes, accept):
+    """Step-0 decisions forced 2e-14 .. 9e-14 from their thresholds (inner hops
+    through solved per-site barriers; an injection and an extraction through a
+    solved electrode rate on open rails): the GPU logs exactly the oracle's
+    entries, field by field, and every forced one among them, on both accept
+    paths and on one-rail-per-warp, several-rails-per-warp and two-words-per-
+    lane shapes; trajectories stay bit-exact."""
+    dev, V, occ0, Ea, targets = forced_device(R, L, electrodes, seed=R * 1000 + L)
+    *_, lg = _compare(kmc, dev, V, occ0, Ea=Ea, accept=accept)
+    got = {(int(e["rail"]), int(e["step"]), int(e["site"]), int(e["dir"]), int(e["kind"]))
+           for e in lg}
+    for t in targets:
+        assert t in got, t
+
+
+def test_rail_shards_reproduce_the_whole_device(kmc):
+    """A device split by rails into parts with rail_base (the multi-GPU
+    partition) advances exactly the rows of the whole device: occupancy,
+    per-rail current, and traces that sum to the whole device's."""
+    R, L = 40, 300
+    dev = _dev(R=R, L=L, Z=10, electrodes=1, k_e=2e6, rho_e=0.3, seed=31, instance=4)
+    Ea = W.normal_barriers(R, L, 0.40, 0.02, seed=8)
+    V = W.triangle_protocol(3.0, 100, 2)
+    whole = kmc.Sim(dev, V, init_mode=1, fill=0.3, Ea_site=Ea)
+    whole.step_n(len(V))
+    Jw, Zw = whole.traces()
+    occ_w, jr_w = whole.occupancy(), whole.rail_current()
+    whole.close()
+    J = np.zeros_like(Jw)
+    Zc = np.zeros_like(Zw)
+    for r0, r1 in [(0, 13), (13, 14), (14, 40)]:
+        part = dict(dev, R=r1 - r0, rail_base=r0)
+        sim = kmc.Sim(part, V, init_mode=1, fill=0.3, Ea_site=Ea[r0:r1])
+        sim.step_n(len(V))
+        j, z = sim.traces()
+        J += j
+        Zc += z
+        assert np.array_equal(sim.occupancy(), occ_w[r0:r1])
+        assert np.array_equal(sim.rail_current(), jr_w[r0:r1])
+        sim.close()
+    assert np.array_equal(J, Jw) and np.array_equal(Zc, Zw)
+    # the oracle advances a part by the same global rail indices
+    part = dict(dev, R=27, rail_base=13)
+    occ_p = oracle.init_occupancy(part, 1, fill=0.3)
+    orc = oracle.OracleSim(part, V, occ_p, Ea[13:40])
+    orc.step_n(len(V))
+    assert np.array_equal(orc.occ, occ_w[13:40])
+    assert np.array_equal(orc.J_rail, jr_w[13:40])
+
+
 def test_hysteresis_device_sampled_rails_full_size(kmc):
     """65,536 x 1,024 device, per-site barriers, open electrodes, +-2 V sweep:
     the GPU advances the whole device; every 256th rail is re-run on the
@@ -215,6 +296,9 @@ def test_hysteresis_device_sampled_rails_full_size(kmc):
     orc = oracle.OracleSim(wl.device, wl.V, occ_init[ids], wl.Ea_site[ids], rail_ids=ids)
     orc.step_n(n)
     assert np.array_equal(occ_g[ids], orc.occ)
+    Jr = sim.rail_current()
+    assert np.array_equal(Jr[ids], orc.J_rail), "per-rail current of the sampled rails differs"
+    assert Jr.sum() == Jg.sum()
     # the first zone-count row is the initial occupancy summed per zone
     z = np.array([oracle.zone_of(k, wl.device.L, wl.device.Z) for k in range(wl.device.L)])
     assert np.array_equal(Zg[0], np.bincount(z, weights=occ_init.sum(axis=0), minlength=10))
@@ -224,7 +308,9 @@ def test_hysteresis_device_sampled_rails_full_size(kmc):
 def test_hysteresis_device_sampled_rails_whole_protocol(kmc):
     """The same device through its whole protocol (two +-2 V cycles, 2e5
     steps, in the bench's 1,000-step launches): every 256th rail re-run on the
-    oracle matches at every 50,000-step checkpoint."""
+    oracle matches, occupancy and per-rail current, at every 50,000-step
+    checkpoint, and the near-threshold decisions of those rails are logged
+    identically."""
     wl = W.hysteresis_65536x1024(steps_per_cycle=100000, cycles=2)
     n_total, chunk, launch = len(wl.V), 50000, 1000
     assert n_total == 200000
@@ -236,7 +322,12 @@ def test_hysteresis_device_sampled_rails_whole_protocol(kmc):
             sim.step_n(launch)
         orc.step_n(chunk)
         assert np.array_equal(sim.occupancy()[ids], orc.occ), "rails differ by step %d" % t
+        assert np.array_equal(sim.rail_current()[ids], orc.J_rail), \
+            "per-rail current differs by step %d" % t
     assert orc.occ.sum() > 0
+    lg, n_lg = sim.near_threshold_log(with_total=True)
+    assert n_lg == len(lg), "the near-threshold log overflowed"
+    assert_logs_equal(lg[np.isin(lg["rail"], ids)], orc.near_threshold_log())
     sim.close()
 
 

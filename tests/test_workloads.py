@@ -118,3 +118,15 @@ def test_seeded_inputs_are_reproducible():
     assert not np.array_equal(a, W.random_occupancy(7, 33, 0.3, seed=6))
     b = W.normal_barriers(5, 9, 0.4, 0.02, seed=1)
     assert np.array_equal(b, W.normal_barriers(5, 9, 0.4, 0.02, seed=1))
+
+
+def test_barrier_table_rows_of_a_shard_equal_the_whole_table():
+    """A rank generating only its rows of the per-site barrier table gets
+    exactly those rows of the whole device's table (blockwise streams)."""
+    whole = W.normal_barriers(50, 200_000, 0.4, 0.02, seed=3)      # blocks of 20 rows
+    for r0, r1 in [(0, 7), (7, 20), (19, 41), (40, 50), (0, 50)]:
+        part = W.normal_barriers(r1 - r0, 200_000, 0.4, 0.02, seed=3, row0=r0)
+        assert np.array_equal(part, whole[r0:r1])
+    wl = W.hysteresis_65536x1024(R=8, L=64, rail_base=24)
+    assert wl.device.rail_base == 24
+    assert np.array_equal(wl.Ea_site, W.normal_barriers(40, 64, 0.40, 0.02, 1001)[24:32])
