@@ -89,6 +89,19 @@ __device__ __forceinline__ uint4 unpack16(uint32_t b)
                       unpack4((b >> 12) & 0xF));
 }
 
+// Site masks of the 32-site word starting at site s0 of an L-site rail: the
+// sites that exist, site 0, site L-1.  Recomputed where needed rather than
+// held in registers through the step.
+__device__ __forceinline__ uint32_t valid_mask(int s0, int L)
+{
+    return s0 >= L ? 0u : (s0 + 32 <= L ? 0xffffffffu : ((1u << (L - s0)) - 1u));
+}
+__device__ __forceinline__ uint32_t first_mask(int s0) { return s0 == 0 ? 1u : 0u; }
+__device__ __forceinline__ uint32_t last_mask(int s0, int L)
+{
+    return (L - 1 >= s0 && L - 1 < s0 + 32) ? (1u << (L - 1 - s0)) : 0u;
+}
+
 // Conservative integer thresholds on the high 32 bits h of a 64-bit draw w
 // (u = (w >> 11) 2^-53):  h < acc_thr(p_lo) implies u <= p;  h > rej_thr(p_hi)
 // implies u > p, for any p in [p_lo, p_hi].
@@ -123,7 +136,8 @@ struct Layout {
     static constexpr size_t FS = N0S + align16(4 * G);         // int [G]
     static constexpr size_t JR = FS + align16(4 * G);          // int [G]: per-rail current
     static constexpr size_t NDEF = JR + align16(4 * G);        // int [4]
-    static constexpr size_t DEF = NDEF + 16;                   // uint16 [kDeferCap]
+    static constexpr size_t CNT = NDEF + 16;                   // uint32 [4]: draws, moves
+    static constexpr size_t DEF = CNT + 16;                    // uint16 [kDeferCap]
     static constexpr size_t LST = DEF + align16(2 * 64);       // uint16 [LIST]
     static constexpr size_t FIXED = LST + align16(2 * LIST);
     // variable part: rm [G Z + 2 G] (zones, then the two electrode sites of each
@@ -177,8 +191,12 @@ struct WarpSmem {
     // net leftward crossings of each rail of the warp since the last flush
     __device__ int32_t *jr() const { return (int32_t *)(b + Ly::JR); }
     __device__ int32_t *ndef() const { return (int32_t *)(b + Ly::NDEF); }
-    // window mid voltage (FP32), stored next to the deferral counter
+    // window mid voltage (FP32) and band factors (flo, fhi), stored next to
+    // the deferral counter
     __device__ float &vmid_ref() const { return *(float *)(b + Ly::NDEF + 4); }
+    __device__ float2 &band() const { return *(float2 *)(b + Ly::NDEF + 8); }
+    // Philox blocks drawn and hops applied by the warp since the last flush
+    __device__ uint32_t *cnt() const { return (uint32_t *)(b + Ly::CNT); }
     __device__ uint16_t *def() const { return (uint16_t *)(b + Ly::DEF); }
     __device__ uint16_t *list() const { return (uint16_t *)(b + Ly::LST); }
     __device__ uint2 *rm() const { return (uint2 *)(b + Ly::FIXED); }
@@ -355,9 +373,11 @@ __device__ __forceinline__ bool record_move(const WarpSmem<LPR, WPL> &S, const D
 template <int LPR, int WPL, bool GRAD = false>
 __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const SweepArgs *g, int i,
                                             int n_inner, int64_t rail0, uint32_t t,
-                                            const uint8_t *zone_tab, bool persite, float flo,
-                                            float fhi, bool exact, uint32_t xy, uint32_t xw)
+                                            const uint8_t *zone_tab, bool persite, bool exact,
+                                            uint32_t xy, uint32_t xw)
 {
+    const float2 band = S.band();
+    const float flo = band.x, fhi = band.y;
     const uint16_t dsc = S.list()[i];
     const int site = dsc & 0x7FF, g2 = LPR == 32 ? 0 : dsc >> 11;
     const int64_t r2 = rail0 + g2;                      // the rail's row in this device
@@ -623,7 +643,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     // the gradient pass writes no traces: no trace buffer
     const int trace_len = GRAD ? 0 : flush * (1 + Z);
     int32_t *trace = (int32_t *)(smem + (size_t)nwarps * wb);
-    uint8_t *zone_tab = (uint8_t *)(trace + trace_len);
+    // the CTA's running count of each zone, carried from flush to flush
+    int32_t *zrun = trace + trace_len;
+    uint8_t *zone_tab = (uint8_t *)(zrun + (GRAD ? 0 : align16((size_t)4 * Z) / 4));
 
     // ---- per-CTA tables and per-warp staging
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -632,7 +654,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         zone_tab[k] = (uint8_t)z;
     }
     for (int i = threadIdx.x; i < trace_len; i += blockDim.x) trace[i] = 0;
+    if (!GRAD && (int)threadIdx.x < Z) zrun[threadIdx.x] = 0;
     for (int pi = lane; pi < G * Z; pi += 32) S.Np()[pi] = 0;
+    if (lane == 0) {
+        S.cnt()[0] = 0;
+        S.cnt()[1] = 0;
+        S.band() = make_float2(1.0f - a.delta, 1.0f + a.delta);
+    }
     for (int i = lane; i < 32 * WPL; i += 32) {
         S.mvR()[i] = 0;
         S.mvL()[i] = 0;
@@ -681,25 +709,27 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         }
     }
 
-    // ---- per-lane site masks and owned zone boundaries
-    uint32_t vm[WPL], firstm[WPL], lastm[WPL], o[WPL];
-    const uint8_t *row = a.occ + (active ? rail : 0) * a.stride;
+    // ---- the rail's occupancy words: read once from HBM, kept in shared memory
+    //      (S.ow) for the whole launch; only the move phase changes them
+    {
+        const uint8_t *row = a.occ + (active ? rail : 0) * a.stride;
 #pragma unroll
-    for (int j = 0; j < WPL; ++j) {
-        const int s0 = 32 * (wbase + j);
-        vm[j] = s0 >= L ? 0u : (s0 + 32 <= L ? FULL : ((1u << (L - s0)) - 1u));
-        firstm[j] = (s0 == 0) ? 1u : 0u;
-        lastm[j] = (L - 1 >= s0 && L - 1 < s0 + 32) ? (1u << (L - 1 - s0)) : 0u;
-        uint32_t bits = 0;
-        if (active) {
-            if (s0 < a.stride) bits |= pack16(*(const uint4 *)(row + s0));
-            if (s0 + 16 < a.stride) bits |= pack16(*(const uint4 *)(row + s0 + 16)) << 16;
+        for (int j = 0; j < WPL; ++j) {
+            const int s0 = 32 * (wbase + j);
+            uint32_t bits = 0;
+            if (active) {
+                if (s0 < a.stride) bits |= pack16(*(const uint4 *)(row + s0));
+                if (s0 + 16 < a.stride) bits |= pack16(*(const uint4 *)(row + s0 + 16)) << 16;
+            }
+            S.ow()[seg * LPR * WPL + wbase + j] = bits & valid_mask(s0, L);
         }
-        o[j] = bits & vm[j];
     }
-    int zlo = 1, zhi = 0;  // interior boundaries z in [zlo, zhi] lie in this lane's words
+    // interior zone boundaries z in [zlo, zhi] that lie in this lane's words,
+    // packed as zlo | zhi << 8
+    int zb = 1;
     {
         const int lo = 32 * wbase, hi = 32 * (wbase + WPL);
+        int zlo = 1, zhi = 0;
         bool first = true;
         for (int z = 1; z < Z; ++z) {
             const int b = a.bnd[z];
@@ -711,16 +741,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 zhi = z;
             }
         }
+        zb = zlo | (zhi << 8);
     }
     bool dirty = true;      // occupancy changed since the candidate list was built
-    int win_end = 0;        // first step after the current voltage window
-    // band factors: p_lo = p flo <= p <= p fhi = p_hi for every step of the window
-    float flo = 1.0f - a.delta, fhi = 1.0f + a.delta;
     int n_inner = 0, nlist = 0;
-    unsigned n_draw = 0, n_move = 0;
     __syncthreads();
 
-    int zrun = 0;   // flush: this CTA's count of zone threadIdx.x (threads < Z)
     for (int c0 = 0; c0 < n_steps; c0 += flush) {
         const int c1 = min(n_steps, c0 + flush);
         for (int s = c0; s < c1; ++s) {
@@ -731,6 +757,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             // every step even when the occupancy does not
             const bool rebuilt = dirty || a.rule != 0;
             if (rebuilt) {
+                uint32_t o[WPL];
+#pragma unroll
+                for (int j = 0; j < WPL; ++j) o[j] = S.ow()[seg * LPR * WPL + wbase + j];
                 // ---- 1. zone counts: segmented scan of popcounts
                 int cnt = 0;
 #pragma unroll
@@ -744,7 +773,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 const int excl = incl - cnt;
                 const int total = __shfl_sync(FULL, incl, LPR - 1, LPR);
                 int fpart = 0;
-                for (int z = zlo; z <= zhi; ++z) {
+                for (int z = zb & 0xFF; z <= (zb >> 8); ++z) {
                     const int b = a.bnd[z];
                     const int j = (b >> 5) - wbase;
                     const uint32_t below = (1u << (b & 31)) - 1u;
@@ -774,7 +803,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 {
                     uint32_t f[WPL];
 #pragma unroll
-                    for (int j = 0; j < WPL; ++j) f[j] = ~o[j] & vm[j];
+                    for (int j = 0; j < WPL; ++j) f[j] = ~o[j] & valid_mask(32 * (wbase + j), L);
                     const uint32_t f_prev = __shfl_up_sync(FULL, f[WPL - 1], 1, LPR);
                     const uint32_t f_next = __shfl_down_sync(FULL, f[0], 1, LPR);
 #pragma unroll
@@ -783,9 +812,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                                                   : (sl > 0 ? (f_prev >> 31) : (open ? 1u : 0u));
                         const uint32_t cn = j < WPL - 1 ? (f[j < WPL - 1 ? j + 1 : 0] & 1u)
                                                         : (sl < LPR - 1 ? (f_next & 1u) : 0u);
+                        const int s0 = 32 * (wbase + j);
+                        const uint32_t firstm = first_mask(s0), lastm = last_mask(s0, L);
                         uint32_t fL = (f[j] << 1) | cp;
                         uint32_t fR = (f[j] >> 1) | (cn << 31);
-                        if (open) fR |= lastm[j];
+                        if (open) fR |= lastm;
                         // brick-wall rule: only bonds (b, b+1) with b = t (mod 2) are
                         // active; a site of the parity of t faces its active bond on
                         // the right, the others on the left (site parity = bit parity)
@@ -799,15 +830,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         }
                         // empty electrode sites: the right bit of site 0 and the left bit
                         // of site L-1 mark an injection trial, the other bits are clear
-                        const uint32_t e0 = firstm[j] & ~o[j], eL = lastm[j] & ~o[j];
+                        const uint32_t e0 = firstm & ~o[j], eL = lastm & ~o[j];
                         fR = (fR & ~(e0 | eL)) | (inj0 ? e0 : 0u);
                         fL = (fL & ~(e0 | eL)) | (injL ? eL : 0u);
                         const int wi = seg * LPR * WPL + wbase + j;
                         S.fR()[wi] = fR;
                         S.fL()[wi] = fL;
-                        S.ow()[wi] = o[j];
                         uint32_t c = o[j] & (fL | fR);
-                        if (open) c &= ~(firstm[j] | lastm[j]);
+                        if (open) c &= ~(firstm | lastm);
                         cand[j] = active ? c : 0u;
                     }
                 }
@@ -841,7 +871,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     if (sl == 0) S.list()[n_inner + 2 * seg] = tag;
 #pragma unroll
                     for (int j = 0; j < WPL; ++j)
-                        if (lastm[j]) S.list()[n_inner + 2 * seg + 1] = (uint16_t)(tag | (L - 1));
+                        if (last_mask(32 * (wbase + j), L))
+                            S.list()[n_inner + 2 * seg + 1] = (uint16_t)(tag | (L - 1));
                 }
                 nlist = n_inner + (open ? 2 * nact : 0);
                 __syncwarp();
@@ -849,9 +880,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
 
             // ---- 2. field and FP32 decision bands per (rail, zone), valid for
             //         every step of the voltage window while the occupancy holds
-            if (dirty || s >= win_end) {
-                if (s >= win_end) {
-                    win_end = min(s + VWIN, n_steps);
+            const bool win_start = (s & (VWIN - 1)) == 0;   // windows of VWIN steps from c0 = 0
+            if (dirty || win_start) {
+                if (win_start) {
+                    const int win_end = min(s + VWIN, n_steps);
                     const int k = min(lane, win_end - 1 - s);
                     const double v = a.V[t + k];
                     float vlo = __double2float_rd(v), vhi = __double2float_ru(v);
@@ -867,11 +899,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     // errors (about 1e-5 relative for |x| <= 40) are covered by delta.
                     const float h = 0.5f * (vhi - vlo) * a.inv_LkT;
                     const float eh = __expf(h) * (1.0f + 1.0f / 65536.0f);
-                    fhi = (1.0f + a.delta) * eh;
-                    flo = (1.0f - a.delta) / eh;
+                    // every lane writes the same values and reads back its own
+                    S.band() = make_float2((1.0f - a.delta) / eh, (1.0f + a.delta) * eh);
                     S.vmid_ref() = 0.5f * (vlo + vhi);
                 }
                 const float Vf = S.vmid_ref();
+                const float2 band = S.band();
+                const float flo = band.x, fhi = band.y;
                 for (int pi = lane; pi < G * Z; pi += 32) {
                     const int g2 = pi / Z;
                     const int z = pi - g2 * Z;
@@ -957,7 +991,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             }
             if (lane == 0) {
                 S.ndef()[0] = 0;
-                n_draw += (unsigned)nlist;
+                S.cnt()[0] += (uint32_t)nlist;
             }
             __syncwarp();
 
@@ -1020,8 +1054,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         }
                         if (slow)
                             moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i, n_inner, rail0, t,
-                                                              zone_tab, persite, flo, fhi, false,
-                                                              xy[q], xw[q]);
+                                                              zone_tab, persite, false, xy[q], xw[q]);
                     }
                 }
             } else {
@@ -1052,8 +1085,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     for (int q = 0; q < kDrawIlpReject; ++q)
                         if (at[q])
                             moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i0 + 32 * q, n_inner, rail0, t,
-                                                              zone_tab, persite, flo, fhi, false, xy[q],
-                                                              xw[q]);
+                                                              zone_tab, persite, false, xy[q], xw[q]);
                 }
             }
             __syncwarp();
@@ -1066,7 +1098,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 for (int k = lane; k < cnt2; k += 32) {
                     const int i = overflow ? k : (int)S.def()[k];
                     moved |= slow_candidate<LPR, WPL, GRAD>(S, a.self, i, n_inner, rail0, t, zone_tab,
-                                                      persite, flo, fhi, true, 0u, 0u);
+                                                      persite, true, 0u, 0u);
                 }
             }
 
@@ -1126,16 +1158,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                                               : (sl > 0 ? (mR_prev >> 31) : (iR ? 1u : 0u));
                     const uint32_t cn = j < WPL - 1 ? (mL[j < WPL - 1 ? j + 1 : 0] & 1u)
                                                     : (sl < LPR - 1 ? (mL_next & 1u) : 0u);
-                    tR[j] = ((mR[j] << 1) | cp) & vm[j];
-                    tL[j] = ((mL[j] >> 1) | (cn << 31)) & vm[j];
-                    if (iL) tL[j] |= lastm[j];
+                    const int s0 = 32 * (wbase + j);
+                    const uint32_t vm = valid_mask(s0, L);
+                    tR[j] = ((mR[j] << 1) | cp) & vm;
+                    tL[j] = ((mL[j] >> 1) | (cn << 31)) & vm;
+                    if (iL) tL[j] |= last_mask(s0, L);
                     cf[j] = tR[j] & tL[j];
                 }
                 const uint32_t c_prev = __shfl_up_sync(FULL, cf[WPL - 1], 1, LPR);
                 const uint32_t c_next = __shfl_down_sync(FULL, cf[0], 1, LPR);
-                int Jl = 0;
+                int Jl = 0, nm = 0;
 #pragma unroll
                 for (int j = 0; j < WPL; ++j) {
+                    const int s0 = 32 * (wbase + j);
+                    const uint32_t lastm = last_mask(s0, L);
+                    const int wi = seg * LPR * WPL + wbase + j;
                     const uint32_t cn = j < WPL - 1 ? (cf[j < WPL - 1 ? j + 1 : 0] & 1u)
                                                     : (sl < LPR - 1 ? (c_next & 1u) : 0u);
                     const uint32_t cp = j > 0 ? (cf[j > 0 ? j - 1 : 0] >> 31)
@@ -1145,17 +1182,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     tR[j] &= ~cf[j];
                     tL[j] &= ~cf[j];
                     Jl += __popc(mL[j]) - __popc(mR[j]);
-                    o[j] = (o[j] & ~(mR[j] | mL[j])) | tR[j] | tL[j];
-                    n_move += (unsigned)(__popc(mR[j]) + __popc(mL[j]));
-                    if (iR && firstm[j] && !(cf[j] & 1u)) {          // injected at site 0
+                    S.ow()[wi] = (S.ow()[wi] & ~(mR[j] | mL[j])) | tR[j] | tL[j];
+                    nm += __popc(mR[j]) + __popc(mL[j]);
+                    if (iR && s0 == 0 && !(cf[j] & 1u)) {            // injected at site 0
                         Jl -= 1;
-                        n_move += 1;
+                        nm += 1;
                     }
-                    if (iL && lastm[j] && !(cf[j] & lastm[j])) {     // injected at L-1
+                    if (iL && lastm && !(cf[j] & lastm)) {           // injected at L-1
                         Jl += 1;
-                        n_move += 1;
+                        nm += 1;
                     }
                 }
+                nm = __reduce_add_sync(FULL, nm);
+                if (lane == 0) S.cnt()[1] += (uint32_t)nm;
                 __syncwarp();
 #pragma unroll
                 for (int j = 0; j < WPL; ++j) {
@@ -1215,17 +1254,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         if ((int)threadIdx.x < Z) {
             // thread z carries the CTA's count of zone z from chunk to chunk
             const int z = threadIdx.x;
+            int run = zrun[z];
             for (int i = 0; i < c1 - c0; ++i) {
-                zrun += trace[i * (1 + Z) + 1 + z];
+                run += trace[i * (1 + Z) + 1 + z];
                 trace[i * (1 + Z) + 1 + z] = 0;
-                if (zrun != 0)
-                    atomicAdd(&a.Zc[(t0 + c0 + i) * Z + z], (unsigned long long)(long long)zrun);
+                if (run != 0)
+                    atomicAdd(&a.Zc[(t0 + c0 + i) * Z + z], (unsigned long long)(long long)run);
             }
+            zrun[z] = run;
         }
-        const unsigned m = __reduce_add_sync(FULL, n_move);
         if (lane == 0) {
-            if (n_draw) atomicAdd(&a.counters[0], (unsigned long long)n_draw);
-            if (m) atomicAdd(&a.counters[2], (unsigned long long)m);
+            const uint32_t nd = S.cnt()[0], nmv = S.cnt()[1];
+            if (nd) atomicAdd(&a.counters[0], (unsigned long long)nd);
+            if (nmv) atomicAdd(&a.counters[2], (unsigned long long)nmv);
+            S.cnt()[0] = 0;
+            S.cnt()[1] = 0;
         }
         // the rail's current of this chunk (at most (L + 1) flush per rail: no
         // int32 overflow) into its int64 total; each rail belongs to one warp
@@ -1234,7 +1277,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             if (v != 0) a.Jr[rail] += v;
             S.jr()[seg] = 0;
         }
-        n_draw = n_move = 0;
         __syncthreads();
     }
 
@@ -1250,8 +1292,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
 #pragma unroll
         for (int j = 0; j < WPL; ++j) {
             const int s0 = 32 * (wbase + j);
-            if (s0 < a.stride) *(uint4 *)(wrow + s0) = unpack16(o[j] & 0xFFFFu);
-            if (s0 + 16 < a.stride) *(uint4 *)(wrow + s0 + 16) = unpack16(o[j] >> 16);
+            const uint32_t o = S.ow()[seg * LPR * WPL + wbase + j];
+            if (s0 < a.stride) *(uint4 *)(wrow + s0) = unpack16(o & 0xFFFFu);
+            if (s0 + 16 < a.stride) *(uint4 *)(wrow + s0 + 16) = unpack16(o >> 16);
         }
     }
 }
@@ -1495,7 +1538,8 @@ size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bo
     else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, acc);
     else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, acc);
     else wb = Layout<32, 1>::bytes(Z, acc);
-    return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) + align16((size_t)L);
+    return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) +
+           align16(sizeof(int32_t) * (size_t)Z) + align16((size_t)L);
 }
 
 size_t grad_smem_bytes(int lpr, int wpl, int Z, int L, int warps)
