@@ -457,6 +457,27 @@ int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss
     ga.alpha = p.alpha_V;
     const double kT = 8.6173e-5 * p.T_K;
     ga.tdev_kT = ((double)L * p.site_spacing_nm) * kT;
+    // exp tables of the integer zone sums: |cm m| <= kappa alpha / kT over
+    // |m| <= 2 L^2; built once per handle, used while every factor is finite
+    ga.etL = ga.etH = nullptr;
+    ga.etM = 0;
+    const double ka = p.kappa * p.alpha_V;
+    if (fabs(ka) / kT < 600.0) {
+        const int32_t M = (int32_t)(2 * L * L);
+        const int32_t nH = 2 * M / 1024 + 2;
+        if (!h->g_etab) {
+            h->g_etab = (double *)h->alloc(sizeof(double) * (size_t)(1024 + nH));
+            if (!h->g_etab) return fail(KMC_E_NOMEM, "device allocation failed (exp tables)");
+        }
+        if (h->g_etM != M) {
+            const double cm = ka / (2.0 * (double)L * (double)L * kT);
+            CK(setup_exp_tables(cm, M, h->g_etab, h->g_etab + 1024, nH, s), "exp tables");
+            h->g_etM = M;
+        }
+        ga.etL = h->g_etab;
+        ga.etH = h->g_etab + 1024;
+        ga.etM = M;
+    }
     CK(cudaMemcpyAsync(h->g_args_dev, &ga, sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
        "copy args");
     ga.t0 = 0;

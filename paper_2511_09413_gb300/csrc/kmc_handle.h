@@ -55,6 +55,8 @@ struct kmc_handle {
     double *g_out = nullptr;                  // [8] sums and standard errors
     unsigned long long *g_misc = nullptr;     // log count and counters of the replay
     kmc::SweepArgs *g_args_dev = nullptr;
+    double *g_etab = nullptr;                 // exp tables of the zone sums (1024 + nH doubles)
+    int32_t g_etM = -1;                       // their range, or -1 when not built
 
     kmc::SweepArgs args{};
     kmc::SweepLaunch launch{};

@@ -79,6 +79,13 @@ struct SweepArgs {
     double *gstate;                      // [R][kGradState] per-rail accumulators
     double alpha;                        // space-charge volts per excess ion
     double tdev_kT;                      // t_dev kB T (d ln B / d kappa denominator)
+    // exp(cm m) for the integer zone sums m = L (Pb_z + Pb_z+1) - F in [-etM, etM]
+    // as etH[(m + etM) >> 10] * etL[(m + etM) & 1023], cm = kappa alpha / (2 L^2 kT)
+    // (null: the gradient pass evaluates exp directly)
+    const double *etL;                   // [1024]
+    const double *etH;                   // [2 etM / 1024 + 1]
+    int32_t etM;
+    int32_t et_pad;
 };
 
 // Per-rail state of the gradient pass: cumulative inner-trial weight W (the
@@ -161,5 +168,8 @@ cudaError_t setup_count_keys(const kmc_params &p, uint64_t key_bound, int mode, 
                              unsigned long long *count, cudaStream_t s);
 cudaError_t setup_mark_smallest(const kmc_params &p, uint64_t key_star, int64_t idx_star,
                                 int select_none, uint8_t *occ, int64_t stride, cudaStream_t s);
+// exp(cm (j 1024 - M)) for j < nH into etH and exp(cm i) for i < 1024 into etL
+cudaError_t setup_exp_tables(double cm, int32_t M, double *etL, double *etH, int32_t nH,
+                             cudaStream_t s);
 
 }  // namespace kmc

@@ -179,6 +179,14 @@ __global__ void mark_smallest_kernel(const kmc_params p, uint64_t key_star, int6
     }
 }
 
+// Tables of the gradient pass: exp(cm m) = etH[(m + M) >> 10] etL[(m + M) & 1023].
+__global__ void exp_table_kernel(double cm, int32_t M, double *etL, double *etH, int32_t nH)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 1024) etL[i] = exp(__dmul_rn(cm, (double)i));
+    if (i < nH) etH[i] = exp(__dmul_rn(cm, (double)((int64_t)i * 1024 - M)));
+}
+
 int grid_for(int64_t n, int block)
 {
     int64_t g = (n + block - 1) / block;
@@ -214,6 +222,14 @@ cudaError_t setup_p0_bounds(const double *P0, int32_t R, int32_t L, int32_t Z, c
 cudaError_t setup_p0_float(const double *P0, int64_t n, float *out, cudaStream_t s)
 {
     p0_float_kernel<<<grid_for(n, 256), 256, 0, s>>>(P0, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t setup_exp_tables(double cm, int32_t M, double *etL, double *etH, int32_t nH,
+                             cudaStream_t s)
+{
+    const int n = nH > 1024 ? nH : 1024;
+    exp_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(cm, M, etL, etH, nH);
     return cudaGetLastError();
 }
 

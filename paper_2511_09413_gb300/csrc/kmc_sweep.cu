@@ -208,7 +208,8 @@ struct WarpSmem {
     __device__ uint32_t *accR() const { return (uint32_t *)(b + goff); }
     __device__ uint32_t *accL() const { return (uint32_t *)(b + goff + align16(4 * Ly::W)); }
     __device__ uint8_t *gbase() const { return b + goff + 2 * align16(4 * Ly::W); }
-    __device__ double *gQ() const { return (double *)gbase(); }
+    // exp(gXV ka D'_z): the background factor of B_z (exp tables on)
+    __device__ double *gEe() const { return (double *)gbase(); }
     __device__ double *gCz() const { return (double *)(gbase() + gzq); }
     __device__ double2 *gP() const { return (double2 *)(gbase() + 2 * gzq); }
     __device__ double2 *gR1() const { return (double2 *)(gbase() + 4 * gzq); }
@@ -441,14 +442,17 @@ __device__ __forceinline__ double trial_weight(int A, int n, double p, double r1
 // from the step-start masks ow, fR, fL and the accepted-trial masks; the
 // electrode trials of the two boundary sites are added one by one.  Lane sl
 // of rail slot seg takes zones sl, sl + W2, ... (W2, a power of two <= LPR,
-// lanes per rail take part) and the partial sums are reduced over them.  In
-// lane sl == 0 it returns Ws, the summed inner-trial weight (times
-// d ln P0 / d theta it is the Ea and nu score), Ks, the kappa score with
-// d ln p / d kappa = (s - B/(1+B)) d ln B / d kappa (s = 1 right, 0 left),
-// and Es, the innovation of the rail's current (left trials' a - p minus
-// right trials' a - p).  The per-zone probabilities (Eqs. 3-6, FP64, the
-// oracle's operation order) are cached until the rail's zone counts or V
-// change.
+// lanes per rail take part) and returns its own zones' Ws, the summed
+// inner-trial weight (times d ln P0 / d theta it is the Ea and nu score), and
+// Ks, the kappa score with d ln p / d kappa = (s - B/(1+B)) d ln B / d kappa
+// (s = 1 right, 0 left); Es, the innovation of the rail's current (left
+// trials' a - p minus right trials' a - p), is summed over the rail's lanes.
+// The per-zone probabilities (Eqs. 3-6, FP64) are cached until the rail's
+// zone counts or V change.  With the exp tables,
+//   B_z = exp(gXV V) exp(gXV ka D'_z) exp(cm m_z),  m_z = L (Pb_z + Pb_z+1) - F,
+// three factors of which only the last changes with the zone counts, looked
+// up by the integer m_z; the probabilities and the reciprocals 1/(1+B),
+// 1/(1-p_R), 1/(1-p_L) then take one FP64 reciprocal.
 template <int LPR, int WPL>
 __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSmem<LPR, WPL> &S,
                                                 uint32_t t, int nact, bool open, int seg, int sl,
@@ -469,6 +473,7 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
         Pc[Z + 1] = changed ? 1 : 0;
         if (changed) {
             for (int z = 0; z <= Z; ++z) Pc[z] = Pb[z];
+            if (!(rs[6] == V)) rs[15] = exp(__dmul_rn(gXV, V));   // exp(gXV V)
             rs[6] = V;
         }
     }
@@ -477,35 +482,43 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
     if (act && sl < W2) {
         double *rs = S.gS() + seg * 16;
         const bool changed = S.gPb()[seg * (Z + 2) + Z + 1] != 0;
+        const bool tabled = a.etL != nullptr && fabs(__dmul_rn(gXV, V)) < 600.0;
         for (int z = sl; z < Z; z += W2) {
             const int pi = seg * Z + z;
             if (changed) {
-                // Q_z - Qbar (S2.1.8) = (Pb_z + Pb_z+1 - F / L) / 2 - D'_z with the
-                // rail's F = sum_z w_z (Pb_z + Pb_z+1) and the per-tile constant D'_z
+                // Q_z - Qbar (S2.1.8) = m_z / (2 L) - D'_z with the integer
+                // m_z = L (Pb_z + Pb_z+1) - F, F = sum_z w_z (Pb_z + Pb_z+1)
                 const int32_t *Pb = S.Pb() + seg * (Z + 1);
-                const double h = __dsub_rn((double)(Pb[z] + Pb[z + 1]),
-                                           __dmul_rn((double)S.Fs()[seg], gInvL));
-                const double dq = __fma_rn(0.5, h, -S.gCz()[pi]);
-                const double dV = __fma_rn(-K.ka, dq, V);
-                const double B = exp(__dmul_rn(dV, gXV));            // Eqs. 3-4
-                // 1/(1+B), 1/(1-p_R), 1/(1-p_L) from one division
-                const double x1 = __dadd_rn(1.0, B);
-                const double pL = __ddiv_rn(K.P0, x1);                // Eq. 5
-                const double pR = __dmul_rn(pL, B);                   // Eq. 6
-                const double x2 = __dsub_rn(1.0, pR), x3 = __dsub_rn(1.0, pL);
-                const double x23 = __dmul_rn(x2, x3);
+                const int m = L * (Pb[z] + Pb[z + 1]) - S.Fs()[seg];
+                const double dq = __fma_rn(0.5 * gInvL, (double)m, -S.gCz()[pi]);
+                double B;                                             // Eqs. 3-4
+                if (tabled) {
+                    const int u = m + a.etM;
+                    B = __dmul_rn(__dmul_rn(rs[15], S.gEe()[pi]),
+                                  __dmul_rn(__ldg(a.etH + (u >> 10)), __ldg(a.etL + (u & 1023))));
+                } else {
+                    B = exp(__dmul_rn(__fma_rn(-K.ka, dq, V), gXV));
+                }
                 const double c = __dmul_rn(gKC, dq);                 // d ln B / d kappa
+                // x1 = 1 + B; y2 = x1 (1 - p_R), y3 = x1 (1 - p_L) with p_L = P0 / x1
+                const double x1 = __dadd_rn(1.0, B);
+                const double y2 = __fma_rn(-K.P0, B, x1), y3 = __dsub_rn(x1, K.P0);
+                const double y23 = __dmul_rn(y2, y3);
                 double inv, r1R, r1L;
-                if (x23 > 0.0) {
-                    const double rp = __drcp_rn(__dmul_rn(x1, x23));
-                    inv = __dmul_rn(x23, rp);
-                    r1R = __dmul_rn(__dmul_rn(x1, x3), rp);
-                    r1L = __dmul_rn(__dmul_rn(x1, x2), rp);
+                if (y23 > 0.0) {
+                    const double rp = __drcp_rn(__dmul_rn(x1, y23));    // 1 / (x1 y2 y3)
+                    const double x1rp = __dmul_rn(x1, rp);
+                    inv = __dmul_rn(y23, rp);
+                    r1R = __dmul_rn(__dmul_rn(x1, y3), x1rp);          // x1 / y2
+                    r1L = __dmul_rn(__dmul_rn(x1, y2), x1rp);          // x1 / y3
                 } else {                                               // a certain trial
                     inv = __drcp_rn(x1);
-                    r1R = pR < 1.0 ? __drcp_rn(x2) : 0.0;
-                    r1L = pL < 1.0 ? __drcp_rn(x3) : 0.0;
+                    const double pL0 = __dmul_rn(K.P0, inv), pR0 = __dmul_rn(pL0, B);
+                    r1R = pR0 < 1.0 ? __drcp_rn(__dsub_rn(1.0, pR0)) : 0.0;
+                    r1L = pL0 < 1.0 ? __drcp_rn(__dsub_rn(1.0, pL0)) : 0.0;
                 }
+                const double pL = __dmul_rn(K.P0, inv);                // Eq. 5
+                const double pR = __dmul_rn(pL, B);                    // Eq. 6
                 S.gP()[pi] = make_double2(pR, pL);
                 S.gR1()[pi] = make_double2(r1R, r1L);
                 S.gPQ()[pi] = make_double2(__dmul_rn(pR, r1R), __dmul_rn(pL, r1L));
@@ -554,8 +567,10 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 const double wL = trial_weight(aL, nL, p.y, r1.y, q.y);
                 Wp = __dadd_rn(Wp, __dadd_rn(wR, wL));
                 Kp = __fma_rn(wR, dk.x, __fma_rn(wL, dk.y, Kp));
-                Ep = __dadd_rn(Ep, __fma_rn(-(double)nL, p.y, (double)aL));
-                Ep = __dsub_rn(Ep, __fma_rn(-(double)nR, p.x, (double)aR));
+                // left trials' a - p minus right trials' a - p: the integer part
+                // aL - aR and nR p_R - nL p_L
+                Ep = __dadd_rn(Ep, __fma_rn((double)nR, p.x,
+                                            __fma_rn(-(double)nL, p.y, (double)(aL - aR))));
             }
             if (open && z == 0) {
                 const double dkR = S.gDK()[pi].x, dkL = S.gDK()[pi].y;
@@ -586,12 +601,8 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
             }
         }
     }
-    // reduce over the W2 lanes of each rail slot (lane sl == 0 holds the sums)
-    for (int off = W2 >> 1; off >= 1; off >>= 1) {
-        Wp = __dadd_rn(Wp, __shfl_xor_sync(FULL, Wp, off, W2));
-        Kp = __dadd_rn(Kp, __shfl_xor_sync(FULL, Kp, off, W2));
-        Ep = __dadd_rn(Ep, __shfl_xor_sync(FULL, Ep, off, W2));
-    }
+    // the rail's innovation, summed over its W2 zone lanes
+    for (int off = W2 >> 1; off >= 1; off >>= 1) Ep = __dadd_rn(Ep, __shfl_xor_sync(FULL, Ep, off, W2));
     Ws = Wp;
     Ks = Kp;
     Es = Ep;
@@ -674,6 +685,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     while (gW2 < Z && gW2 < LPR) gW2 <<= 1;
     // 1 / L; dV_z -> ln B_z = -dV_z d / (t_dev kT) (Eqs. 3-4); dq -> d ln B_z / d kappa
     double gInvL = 0.0, gXV = 0.0, gKC = 0.0;
+    // gradient pass: this lane's share of the rail's cumulative inner-trial
+    // weight W, kappa score K and estimator sums G_W, G_K (its zones' terms;
+    // the rail's values are the sums over its lanes, formed at the end)
+    double aW = 0.0, aK = 0.0, aGW = 0.0, aGK = 0.0;
     if constexpr (GRAD) {
         gInvL = 1.0 / (double)L;
         gXV = -(a.K->d / a.K->t_dev) / a.K->kT;
@@ -692,12 +707,24 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 S.gCz()[seg * Z + z] = D;
             }
             const double mean = acc / (double)L;
-            for (int z = 0; z < Z; ++z) S.gCz()[seg * Z + z] -= mean;
+            for (int z = 0; z < Z; ++z) {
+                S.gCz()[seg * Z + z] -= mean;
+                // the background factor exp(gXV ka D'_z) of B_z (exp tables)
+                if (a.etL) S.gEe()[seg * Z + z] = exp(__dmul_rn(__dmul_rn(gXV, a.K->ka),
+                                                                  S.gCz()[seg * Z + z]));
+            }
         }
         if (sl == 0) S.gS()[seg * 16 + 6] = __longlong_as_double(0x7FF8000000000000ll);  // no cache
-        if (sl == 0)
-            for (int i = 0; i < kGradState; ++i)
-                S.gS()[seg * 16 + i] = active ? a.gstate[rail * kGradState + i] : 0.0;
+        if (sl == 0 && active) {
+            const double *g0 = a.gstate + rail * kGradState;
+            aW = g0[0];
+            aK = g0[1];
+            aGW = g0[2];
+            aGK = g0[3];
+            S.gS()[seg * 16 + 4] = g0[4];
+        } else if (sl == 0) {
+            S.gS()[seg * 16 + 4] = 0.0;
+        }
     }
     for (int i = lane; i < 2 * G; i += 32) S.inj()[i] = 0;
     if (sl == 0) S.N0s()[seg] = active ? a.N0[rail] : 0;
@@ -1108,12 +1135,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 double Ws, Ks, Es;
                 grad_step_score<LPR, WPL>(a, S, t, nact, open, seg, sl, gW2, gInvL, gXV, gKC,
                                           Ws, Ks, Es);
+                // coefficient of the score before this step: the zone counts at
+                // the start of step t, less the current's innovation (a control
+                // variate of zero mean); formed by the rail's first lane, applied
+                // by every lane to its share of the score
+                double d = 0.0;
                 if (sl == 0 && seg < nact) {
-                    double *st = S.gS() + seg * 16;      // W, K, G_W, G_K, G_1
-                    // coefficient of the score before this step: the zone counts at
-                    // the start of step t, less the current's innovation (a control
-                    // variate of zero mean)
-                    double d = 0.0;
                     if (a.fZa) {
                         double fZ = -a.fZb[t];
                         for (int z = 0; z < Z; ++z) {
@@ -1123,14 +1150,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         d = fZ;
                     }
                     if (a.wJ) d = __fma_rn(-a.wJ[t], Es, d);
-                    if (d != 0.0) {
-                        st[2] = __fma_rn(d, st[0], st[2]);
-                        st[3] = __fma_rn(d, st[1], st[3]);
-                        st[4] = __dadd_rn(st[4], d);
-                    }
-                    st[0] = __dadd_rn(st[0], Ws);
-                    st[1] = __dadd_rn(st[1], Ks);
+                    if (d != 0.0) S.gS()[seg * 16 + 4] = __dadd_rn(S.gS()[seg * 16 + 4], d);   // G_1
                 }
+                d = __shfl_sync(FULL, d, 0, LPR);
+                if (d != 0.0) {
+                    aGW = __fma_rn(d, aW, aGW);
+                    aGK = __fma_rn(d, aK, aGK);
+                }
+                aW = __dadd_rn(aW, Ws);
+                aK = __dadd_rn(aK, Ks);
 #pragma unroll
                 for (int j = 0; j < WPL; ++j) {
                     S.accR()[seg * LPR * WPL + wbase + j] = 0u;
@@ -1229,15 +1257,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 }
             }
             if constexpr (GRAD) {
-                // the current of step t pairs with the score of steps <= t
-                if (a.wJ && sl == 0 && seg < nact) {
+                // the current of step t pairs with the score of steps <= t;
+                // every lane of the rail holds its J_t (Jrail)
+                if (a.wJ) {
                     const double2 ab = a.fJab[t];
                     if (ab.x != 0.0 || ab.y != 0.0) {
-                        double *st = S.gS() + seg * 16;
                         const double fJ = __fma_rn(ab.x, (double)Jrail, -ab.y);
-                        st[2] = __fma_rn(fJ, st[0], st[2]);
-                        st[3] = __fma_rn(fJ, st[1], st[3]);
-                        st[4] = __dadd_rn(st[4], fJ);
+                        aGW = __fma_rn(fJ, aW, aGW);
+                        aGK = __fma_rn(fJ, aK, aGK);
+                        if (sl == 0 && seg < nact)
+                            S.gS()[seg * 16 + 4] = __dadd_rn(S.gS()[seg * 16 + 4], fJ);
                     }
                 }
             }
@@ -1281,9 +1310,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     }
 
     if constexpr (GRAD) {
-        if (active && sl == 0)
-            for (int i = 0; i < kGradState; ++i)
-                a.gstate[rail * kGradState + i] = S.gS()[seg * 16 + i];
+        // the rail's W, K, G_W, G_K: sums of its lanes' shares
+#pragma unroll
+        for (int off2 = LPR / 2; off2 >= 1; off2 >>= 1) {
+            aW = __dadd_rn(aW, __shfl_xor_sync(FULL, aW, off2, LPR));
+            aK = __dadd_rn(aK, __shfl_xor_sync(FULL, aK, off2, LPR));
+            aGW = __dadd_rn(aGW, __shfl_xor_sync(FULL, aGW, off2, LPR));
+            aGK = __dadd_rn(aGK, __shfl_xor_sync(FULL, aGK, off2, LPR));
+        }
+        if (active && sl == 0) {
+            double *g0 = a.gstate + rail * kGradState;
+            g0[0] = aW;
+            g0[1] = aK;
+            g0[2] = aGW;
+            g0[3] = aGK;
+            g0[4] = S.gS()[seg * 16 + 4];
+        }
     }
 
     // ---- write the rail back
