@@ -523,6 +523,11 @@ def run_adjoint(args):
         "backward": {"site_updates_per_s": su / t_bwd, "s": t_bwd},
         "observable": float(J[n_write:].mean() / args.replicas),
         "grad": dict(zip(names, g.tolist())), "grad_stderr": dict(zip(names, se.tolist())),
+        # standard error relative to the estimate, and the replicas at which it
+        # would reach 5 % (it falls as 1 / sqrt(replicas): replicas are independent)
+        "grad_rel_stderr": dict(zip(names, (se / np.abs(g)).tolist())),
+        "replicas_for_5pct_stderr": dict(zip(names, np.ceil(
+            args.replicas * (se / np.abs(g) / 0.05) ** 2).astype(int).tolist())),
     }
     if args.fd_groups > 0:
         G = args.fd_groups
@@ -564,6 +569,9 @@ def run_adjoint(args):
             "fd": dict(zip(names, fm.tolist())), "fd_stderr": dict(zip(names, fs.tolist())),
             "z": dict(zip(names, ((lm - fm) / np.hypot(ls, fs)).tolist())),
             "rel_diff": dict(zip(names, (np.abs(lm - fm) / np.abs(fm)).tolist())),
+            # the full-size LR estimate against the differences of the check
+            "lr_full_rel_diff": dict(zip(names, (np.abs(g - fm) / np.abs(fm)).tolist())),
+            "lr_full_z": dict(zip(names, ((g - fm) / np.hypot(se, fs)).tolist())),
             "gpu_s_per_group": {"lr_forward_backward": cost_lr, "fd_two_forwards": cost_fd},
             # GPU time for one entry at equal standard error: FD / LR
             "fd_over_lr_time_at_equal_error": dict(zip(names, (
@@ -650,6 +658,8 @@ def run_fit(args):
     assert np.array_equal(samples, tgt["sample_steps"])
     fit = MaterialFit(devs, V, fills, samples, tgt["target"],
                       stream=torch.cuda.current_stream().cuda_stream)
+    if args.fit_eval or args.fit_loss:
+        return _fit_evaluations(args, fit, devs, tgt, name)
     hist = fit.run(0.40, 1.0, iters=args.fit_iters, lr=(6e-3, 5e-2))
     su = sum(d.R * d.L for d in devs) * fit.n_steps
     t_f = sum(h.seconds_forward for h in hist)
@@ -684,6 +694,50 @@ def run_fit(args):
     return 0
 
 
+def _points(spec):
+    return [tuple(float(x) for x in p.split(",")) for p in spec.split(";") if p.strip()]
+
+
+def _fit_evaluations(args, fit, devs, tgt, name):
+    """Loss and gradient (--fit-eval) or loss alone (--fit-loss) of the fit
+    at given (Ea, kappa) points, without iterating: whether the curves of the
+    protocol determine the hidden parameters."""
+    su = sum(d.R * d.L for d in devs) * fit.n_steps
+    evals = []
+    for Ea, ka in _points(args.fit_eval):
+        st = fit.loss_and_grad(Ea, ka)
+        evals.append({"Ea": Ea, "kappa": ka, "loss": st.loss, "grad": st.grad.tolist(),
+                      "grad_stderr": st.stderr.tolist(), "s_forward": st.seconds_forward,
+                      "s_backward": st.seconds_backward,
+                      "forward_site_updates_per_s": su / st.seconds_forward,
+                      "backward_site_updates_per_s": su / st.seconds_backward})
+    losses = []
+    for Ea, ka in _points(args.fit_loss):
+        loss, G, sec = fit.loss(Ea, ka)
+        losses.append({"Ea": Ea, "kappa": ka, "loss": loss, "s_forward": sec,
+                       "forward_site_updates_per_s": su / sec,
+                       "G_end_mean": float(G[:, -1].mean()),
+                       "G_peak_mean": float(G.max(axis=1).mean())})
+    secs = sum(e["s_forward"] + e.get("s_backward", 0.0) for e in evals + losses)
+    line = {
+        "metric": METRIC + ", batched + adjoint fit evaluations", "value": su * len(evals + losses) / secs,
+        "unit": UNIT, "n_gpus": 1, "steps": len(evals + losses), "warmup": 0,
+        "ms_per_step": 1e3 * secs / max(1, len(evals + losses)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fit_batch", "devices": len(devs),
+                   "sites_total": sum(d.R * d.L for d in devs),
+                   "protocol": "%d pulses of 0.8 V x 0.5 ms, 0.5 ms apart, then %d steps" % (
+                       args.fit_pulses, args.fit_forget),
+                   "time_steps": fit.n_steps, "samples_per_curve": len(fit.sample_steps),
+                   "target": os.path.relpath(name, ROOT) + " (oracle, %d rails per device)" % int(
+                       tgt["rails_per_device"]),
+                   "hidden": {"Ea": float(tgt["Ea"]), "kappa": float(tgt["kappa"])}},
+        "evaluations": evals, "losses": losses,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -697,6 +751,8 @@ def main(argv=None):
     ap.add_argument("--fit-pulses", type=int, default=8)
     ap.add_argument("--fit-forget", type=int, default=8000)
     ap.add_argument("--fit-iters", type=int, default=5)
+    ap.add_argument("--fit-eval", default="", help="fit: 'Ea,kappa;...' points for loss and gradient")
+    ap.add_argument("--fit-loss", default="", help="fit: 'Ea,kappa;...' points for the loss alone")
     ap.add_argument("--replicas", type=int, default=256, help="replicas in the adjoint workload")
     ap.add_argument("--adj-write", type=int, default=10000, help="write-pulse steps (adjoint)")
     ap.add_argument("--adj-relax", type=int, default=50000, help="relaxation steps (adjoint)")

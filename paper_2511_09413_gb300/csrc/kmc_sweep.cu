@@ -427,13 +427,37 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
 // ------------------------------------------------- likelihood-ratio score
 // Summed score weight of n Bernoulli(p) trials of which A succeeded: each
 // trial contributes (a - p) / (1 - p) times d ln p, so the sum is
-// A / (1 - p) - n p / (1 - p) (a certain trial, p >= 1, contributes d ln p).
-// r1 = 1 / (1 - p) and q = p / (1 - p) are kept with p.
-__device__ __forceinline__ double trial_weight(int A, int n, double p, double r1, double q)
+// A r1 - n q with r1 = 1 / (1 - p) and q = p / (1 - p), kept with p; a
+// certain trial (p >= 1) contributes d ln p, and is cached as r1 = 1, q = 0.
+__device__ __forceinline__ double trial_weight(int A, int n, double r1, double q)
 {
-    if (n == 0) return 0.0;
-    if (p >= 1.0) return (double)A;
     return __fma_rn(-(double)n, q, __dmul_rn((double)A, r1));
+}
+// 1 / d for d > 0 (normal, finite) by Newton-Raphson on f(r) = 1/r - d from the
+// hardware approximation (rcp.approx.ftz.f64, about 2^-22 relative): each
+// step r <- r + r (1 - d r) squares the relative error, so two give full FP64
+// accuracy up to a few ulp, enough for score weights.
+__device__ __forceinline__ double recip_newton(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = __fma_rn(-d, r, 1.0);
+    r = __fma_rn(r, e, r);
+    e = __fma_rn(-d, r, 1.0);
+    return __fma_rn(r, e, r);
+}
+
+// Score weight of one electrode trial of probability p, outcome hit, with
+// r1 = 1 / (1 - p) (0 when p >= 1)
+__device__ __forceinline__ double et_weight(int hit, double p, double r1)
+{
+    if (p >= 1.0) return (double)hit;
+    return __fma_rn(-1.0, __dmul_rn(p, r1), __dmul_rn((double)hit, r1));
+}
+// r1 and q of a trial of probability p (cached for inner trials)
+__device__ __forceinline__ double2 trial_factors(double p, double r1_if_uncertain)
+{
+    return p >= 1.0 ? make_double2(1.0, 0.0) : make_double2(r1_if_uncertain, __dmul_rn(p, r1_if_uncertain));
 }
 
 // Score of one step for the rails of a warp (gradient pass).  Trials are
@@ -504,25 +528,30 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 const double x1 = __dadd_rn(1.0, B);
                 const double y2 = __fma_rn(-K.P0, B, x1), y3 = __dsub_rn(x1, K.P0);
                 const double y23 = __dmul_rn(y2, y3);
-                double inv, r1R, r1L;
-                if (y23 > 0.0) {
-                    const double rp = __drcp_rn(__dmul_rn(x1, y23));    // 1 / (x1 y2 y3)
-                    const double x1rp = __dmul_rn(x1, rp);
+                double inv, pL, pR;
+                const double xd = __dmul_rn(x1, y23);
+                if (xd > 1e-300 && xd < 1e300) {                       // both trials uncertain
+                    const double rp = recip_newton(xd);                // 1 / (x1 y2 y3)
+                    const double x1rp = __dmul_rn(x1, rp), x1x1rp = __dmul_rn(x1, x1rp);
                     inv = __dmul_rn(y23, rp);
-                    r1R = __dmul_rn(__dmul_rn(x1, y3), x1rp);          // x1 / y2
-                    r1L = __dmul_rn(__dmul_rn(x1, y2), x1rp);          // x1 / y3
-                } else {                                               // a certain trial
+                    pL = __dmul_rn(K.P0, inv);                          // Eq. 5
+                    pR = __dmul_rn(pL, B);                              // Eq. 6
+                    const double r1R = __dmul_rn(y3, x1x1rp), r1L = __dmul_rn(y2, x1x1rp);  // x1/y2, x1/y3
+                    S.gR1()[pi] = make_double2(r1R, r1L);
+                    S.gPQ()[pi] = make_double2(__dmul_rn(pR, r1R), __dmul_rn(pL, r1L));
+                } else {                                               // a certain trial, or B out of range
                     inv = __drcp_rn(x1);
-                    const double pL0 = __dmul_rn(K.P0, inv), pR0 = __dmul_rn(pL0, B);
-                    r1R = pR0 < 1.0 ? __drcp_rn(__dsub_rn(1.0, pR0)) : 0.0;
-                    r1L = pL0 < 1.0 ? __drcp_rn(__dsub_rn(1.0, pL0)) : 0.0;
+                    pL = __dmul_rn(K.P0, inv);
+                    pR = __dmul_rn(pL, B);
+                    const double2 fR = trial_factors(pR, pR < 1.0 ? __drcp_rn(__dsub_rn(1.0, pR)) : 0.0);
+                    const double2 fL = trial_factors(pL, pL < 1.0 ? __drcp_rn(__dsub_rn(1.0, pL)) : 0.0);
+                    S.gR1()[pi] = make_double2(fR.x, fL.x);
+                    S.gPQ()[pi] = make_double2(fR.y, fL.y);
                 }
-                const double pL = __dmul_rn(K.P0, inv);                // Eq. 5
-                const double pR = __dmul_rn(pL, B);                    // Eq. 6
                 S.gP()[pi] = make_double2(pR, pL);
-                S.gR1()[pi] = make_double2(r1R, r1L);
-                S.gPQ()[pi] = make_double2(__dmul_rn(pR, r1R), __dmul_rn(pL, r1L));
-                S.gDK()[pi] = make_double2(__dmul_rn(inv, c), -__dmul_rn(__dsub_rn(1.0, inv), c));
+                // d ln p / d kappa: right (1 - B/(1+B)) c = inv c, left -(B/(1+B)) c = inv c - c
+                const double dkR = __dmul_rn(inv, c);
+                S.gDK()[pi] = make_double2(dkR, __dsub_rn(dkR, c));
                 if (open && z == 0) {
                     const double pin = __dmul_rn(__dmul_rn(K.E_in, inv), B);   // injection into 0
                     const double pout = __dmul_rn(K.E_out, inv);               // extraction at 0
@@ -563,8 +592,8 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
             }
             if (nR | nL) {
                 const double2 p = S.gP()[pi], r1 = S.gR1()[pi], q = S.gPQ()[pi], dk = S.gDK()[pi];
-                const double wR = trial_weight(aR, nR, p.x, r1.x, q.x);
-                const double wL = trial_weight(aL, nL, p.y, r1.y, q.y);
+                const double wR = trial_weight(aR, nR, r1.x, q.x);
+                const double wL = trial_weight(aL, nL, r1.y, q.y);
                 Wp = __dadd_rn(Wp, __dadd_rn(wR, wL));
                 Kp = __fma_rn(wR, dk.x, __fma_rn(wL, dk.y, Kp));
                 // left trials' a - p minus right trials' a - p: the integer part
@@ -577,11 +606,11 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 const int idx = seg * LPR * WPL;
                 if (S.ow()[idx] & 1u) {        // extraction through the left electrode
                     const int hit = (S.accL()[idx] & 1u) ? 1 : 0;
-                    Kp = __fma_rn(trial_weight(hit, 1, rs[8], rs[12], __dmul_rn(rs[8], rs[12])), dkL, Kp);
+                    Kp = __fma_rn(et_weight(hit, rs[8], rs[12]), dkL, Kp);
                     Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[8]));
                 } else {                       // injection into site 0
                     const int hit = (S.accR()[idx] & 1u) ? 1 : 0;
-                    Kp = __fma_rn(trial_weight(hit, 1, rs[7], rs[11], __dmul_rn(rs[7], rs[11])), dkR, Kp);
+                    Kp = __fma_rn(et_weight(hit, rs[7], rs[11]), dkR, Kp);
                     Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[7]));
                 }
             }
@@ -591,11 +620,11 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 const uint32_t bit = 1u << ((L - 1) & 31);
                 if (S.ow()[idx] & bit) {       // extraction through the right electrode
                     const int hit = (S.accR()[idx] & bit) ? 1 : 0;
-                    Kp = __fma_rn(trial_weight(hit, 1, rs[9], rs[13], __dmul_rn(rs[9], rs[13])), dkR, Kp);
+                    Kp = __fma_rn(et_weight(hit, rs[9], rs[13]), dkR, Kp);
                     Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[9]));
                 } else {                       // injection into site L-1
                     const int hit = (S.accL()[idx] & bit) ? 1 : 0;
-                    Kp = __fma_rn(trial_weight(hit, 1, rs[10], rs[14], __dmul_rn(rs[10], rs[14])), dkL, Kp);
+                    Kp = __fma_rn(et_weight(hit, rs[10], rs[14]), dkL, Kp);
                     Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[10]));
                 }
             }
@@ -1355,9 +1384,10 @@ __global__ void __launch_bounds__(256, ACC ? 4 : 5) sweep_kernel(const SweepArgs
 }
 
 // Gradient pass: the forward sweep replayed from a checkpoint with the
-// likelihood-ratio score accumulated per rail (2 CTAs of 256 threads per SM).
+// likelihood-ratio score accumulated per rail (3 CTAs of 256 threads per SM:
+// 80 registers; 2 CTAs at 128 registers run 5 % slower, 4 at 64 no faster).
 template <int LPR, int WPL>
-__global__ void __launch_bounds__(256, 2) sweep_grad_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, 3) sweep_grad_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const int64_t tile_rail0 = (int64_t)blockIdx.x * (blockDim.x >> 5) * (32 / LPR);

@@ -54,6 +54,28 @@ class MaterialFit:
         self.warps, self.steps_per_launch = warps, steps_per_launch
         self.stream = stream
 
+    def loss(self, Ea: float, kappa: float):
+        """(loss, curves G [devices, samples], forward seconds) at (Ea, kappa),
+        without the backward pass."""
+        import torch
+        devs = [dataclasses.replace(d, Ea=Ea, kappa=kappa) for d in self.devs]
+        n = len(devs)
+        b = K.Batch(devs, [self.V] * n, [1] * n, fills=self.fills, stream=self.stream)
+        try:
+            b.set_launch(self.warps, self.steps_per_launch)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.step_n(self.n_steps)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            G = np.zeros_like(self.target)
+            for i in range(n):
+                _, Zc = b.traces(i)
+                G[i] = Zc[self.sample_steps, 0] / max(float(Zc[0].sum()), 1.0)
+        finally:
+            b.close()
+        return float(((G - self.target) ** 2).sum()), G, t1 - t0
+
     def loss_and_grad(self, Ea: float, kappa: float) -> FitStep:
         import torch
         devs = [dataclasses.replace(d, Ea=Ea, kappa=kappa) for d in self.devs]
