@@ -170,6 +170,19 @@ struct Layout {
     }
 };
 
+// Candidate-list entries (uint16): the site in the low bits and, above it,
+// the rail slot (several rails per warp) or, with one rail per warp, the row
+// of the entry's decision bounds in rm (its zone).  Rails of at most 1,024
+// sites in one word per lane need only 10 site bits, which leaves 6 bits for
+// rows up to G Z + 1, so the electrode entries carry their rows too and the
+// draw loop reads every row straight from the entry.
+template <int LPR, int WPL>
+struct ListCode {
+    static constexpr bool kRow = LPR == 32 && WPL == 1;
+    static constexpr int kShift = kRow ? 10 : 11;
+    static constexpr uint32_t kSite = (1u << kShift) - 1u;
+};
+
 template <int LPR, int WPL>
 struct WarpSmem {
     using Ly = Layout<LPR, WPL>;
@@ -380,7 +393,7 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
     const float2 band = S.band();
     const float flo = band.x, fhi = band.y;
     const uint16_t dsc = S.list()[i];
-    const int site = dsc & 0x7FF, g2 = LPR == 32 ? 0 : dsc >> 11;
+    const int site = dsc & ListCode<LPR, WPL>::kSite, g2 = LPR == 32 ? 0 : dsc >> 11;
     const int64_t r2 = rail0 + g2;                      // the rail's row in this device
     const uint32_t rg = g->rail_base + (uint32_t)r2;    // its global index (Philox, log)
     // the bounded decision needs only the high words (x1, x3) of the draw; the
@@ -917,18 +930,25 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     while (m) {
                         const uint32_t site = base + (uint32_t)(__ffs(m) - 1);
                         // with one rail per warp the rail-slot bits carry the zone
-                        S.list()[pos++] = (uint16_t)(G == 1 ? site | ((uint32_t)zone_tab[site] << 11)
+                        S.list()[pos++] = (uint16_t)(G == 1 ? site | ((uint32_t)zone_tab[site]
+                                                                      << ListCode<LPR, WPL>::kShift)
                                                             : site);
                         m &= m - 1;
                     }
                 }
                 if (open && seg < nact) {
-                    const uint16_t tag = (uint16_t)(seg << 11);
-                    if (sl == 0) S.list()[n_inner + 2 * seg] = tag;
+                    // electrode entries: rows G Z + 2 seg (site 0) and + 1 (site L-1)
+                    // in the entry when it has room, else the rail slot
+                    constexpr bool kRow = ListCode<LPR, WPL>::kRow;
+                    const uint32_t r0 = kRow ? (uint32_t)(G * Z + 2 * seg) << ListCode<LPR, WPL>::kShift
+                                             : (uint32_t)seg << 11;
+                    const uint32_t r1 = kRow ? (uint32_t)(G * Z + 2 * seg + 1) << ListCode<LPR, WPL>::kShift
+                                             : (uint32_t)seg << 11;
+                    if (sl == 0) S.list()[n_inner + 2 * seg] = (uint16_t)r0;
 #pragma unroll
                     for (int j = 0; j < WPL; ++j)
                         if (last_mask(32 * (wbase + j), L))
-                            S.list()[n_inner + 2 * seg + 1] = (uint16_t)(tag | (L - 1));
+                            S.list()[n_inner + 2 * seg + 1] = (uint16_t)(r1 | (uint32_t)(L - 1));
                 }
                 nlist = n_inner + (open ? 2 * nact : 0);
                 __syncwarp();
@@ -1066,11 +1086,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         const int i = i0 + 32 * q;
                         const bool has = i < nlist;
                         const uint16_t d = S.list()[has ? i : i0];
-                        const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
+                        const int site = d & ListCode<LPR, WPL>::kSite, g = G == 1 ? 0 : d >> 11;
                         const uint4 x = philox((uint32_t)site, prail0 + (uint32_t)g, t, instance,
                                                rk0, rk1);
-                        const int ts = i >= n_inner ? G * Z + (i - n_inner)
-                                                    : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]);
+                        const int ts = ListCode<LPR, WPL>::kRow
+                                           ? (int)(d >> ListCode<LPR, WPL>::kShift)
+                                           : (i >= n_inner ? G * Z + (i - n_inner)
+                                                           : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]));
                         th[q] = S.rm4()[ts];
                         xy[q] = x.y;
                         xw[q] = x.w;
@@ -1126,12 +1148,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         // with one rail per warp the rail slot is 0: the rail, step and
                         // instance words are then warp-uniform and the compiler hoists
                         // the parts of the first two Philox rounds that depend only on them
-                        const int site = d & 0x7FF, g = G == 1 ? 0 : d >> 11;
+                        const int site = d & ListCode<LPR, WPL>::kSite, g = G == 1 ? 0 : d >> 11;
                         const uint4 x = philox((uint32_t)site, prail0 + (uint32_t)g, t, instance,
                                                rk0, rk1);
-                        // electrode sites have their own entries after the G Z zone entries
-                        const int ts = i >= n_inner ? G * Z + (i - n_inner)
-                                                    : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]);
+                        // electrode sites have their own rows after the G Z zone rows
+                        const int ts = ListCode<LPR, WPL>::kRow
+                                           ? (int)(d >> ListCode<LPR, WPL>::kShift)
+                                           : (i >= n_inner ? G * Z + (i - n_inner)
+                                                           : (G == 1 ? (d >> 11) : g * Z + zone_tab[site]));
                         const uint2 rm = S.rm()[ts];
                         xy[q] = x.y;
                         xw[q] = x.w;

@@ -144,3 +144,51 @@ def test_device_maps_to_the_same_quantities_on_both_sides():
         assert getattr(q, b) == {"seed": (-5) & 0xFFFFFFFFFFFFFFFF}.get(b, dev.as_dict()[b])
     assert p.init_mode == 1 and p.fill == 0.3 and p.rail_base == 0
     assert kmc.params_from_device(dev.as_dict(), init_mode=0, n_ions=9).n_ions == 9
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(n_rails=(1 << 20) + 1), "KMC_NOALLOC_MAX_RAILS"),
+    (dict(rail_base=-1), "rail_base"),
+    (dict(n_sites=1), "n_sites"),
+    (dict(update_rule=3), "update_rule"),
+])
+def test_noalloc_rejects_bad_parameters_before_touching_a_gpu(lib, bad, code):
+    """kmc_sweep_noalloc checks every argument on the host and returns
+    KMC_E_ARG before any CUDA call: these run without a GPU."""
+    from paper_2511_09413_gb300 import kmc
+    p = _params(**bad)
+    fake = ctypes.c_void_p(1 << 20)              # 16-byte aligned, never dereferenced
+    rc = lib.kmc_sweep_noalloc(ctypes.byref(p), fake, 112, None, fake, 0, 5, fake, fake, None)
+    assert rc == kmc.KMC_E_ARG
+    assert code.encode() in lib.kmc_last_error()
+
+
+def test_noalloc_checks_layout_arguments_on_the_host(lib):
+    from paper_2511_09413_gb300 import kmc
+    p = _params()
+    fake = ctypes.c_void_p(1 << 20)
+    # row stride not a multiple of 16, or shorter than a row
+    assert lib.kmc_sweep_noalloc(ctypes.byref(p), fake, 100, None, fake, 0, 5, fake, fake, None) == kmc.KMC_E_ARG
+    assert lib.kmc_sweep_noalloc(ctypes.byref(p), fake, 96, None, fake, 0, 5, fake, fake, None) == kmc.KMC_E_ARG
+    # occupancy not 16-byte aligned
+    assert lib.kmc_sweep_noalloc(ctypes.byref(p), ctypes.c_void_p((1 << 20) + 8), 112, None, fake, 0, 5,
+                                 fake, fake, None) == kmc.KMC_E_ARG
+    # missing voltage or trace buffers for a non-empty call
+    assert lib.kmc_sweep_noalloc(ctypes.byref(p), fake, 112, None, None, 0, 5, fake, fake, None) == kmc.KMC_E_ARG
+    # zero steps: nothing to do, nothing touched
+    assert lib.kmc_sweep_noalloc(ctypes.byref(p), fake, 112, None, None, 0, 0, None, None, None) == kmc.KMC_OK
+
+
+def test_header_states_the_contracts_it_promises():
+    """The boundary's declarations carry their passages and the no-alloc entry
+    point's undocumented-input rule."""
+    src = open(HEADER).read()
+    step = src[:src.index("int kmc_step_n(")]
+    step = step[step.rindex("/*"):]
+    assert "S2.1.2 - S2.1.7" in step and "Eq. 3" in step and "Eqs. 5-6" in step
+    obs = src[:src.index("int kmc_observables(")]
+    obs = obs[obs.rindex("/* Read observables"):]
+    assert "S3" in obs and "S2.1.7" in obs
+    noalloc = src[src.index("---- Sweep without any device allocation"):src.index("int kmc_sweep_noalloc(")]
+    assert "other than 0 or 1 gives" in noalloc and "undefined results" in noalloc
+    assert "rail_base" in src[src.index("typedef struct kmc_params"):src.index("} kmc_params;")]
