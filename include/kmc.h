@@ -163,8 +163,10 @@ int kmc_near_threshold_log(kmc_handle *h, kmc_log_entry *out, int64_t cap, int64
  * resolved by the exact FP64 path, [2] accepted moves (synchronizes). */
 int kmc_counters(kmc_handle *h, uint64_t out[3]);
 
-/* Launch shape: warps per CTA (1..32, 0 = automatic) and steps between
- * trace flushes (1..1024, 0 = automatic).  Results do not depend on either. */
+/* Launch shape: warps per CTA (1..32, 0 = automatic) and steps between the
+ * warps' flushes of their counters and per-rail current (1..1024, 0 =
+ * automatic; the traces are written as the steps run).  Results do not
+ * depend on either. */
 int kmc_set_launch(kmc_handle *h, int warps_per_cta, int flush_steps);
 
 /* Accept path: mode 1 selects the kernel that also keeps accept-sure bounds

@@ -143,6 +143,9 @@ BatchArgs batch_args(const kmc_batch *b, int n_steps)
     a.n_items = b->n_items;
     a.n_steps = n_steps;
     a.flush = b->flush;
+    a.n_inst = (int32_t)b->dev.size();
+    a.max_z = 1;
+    for (const kmc_handle *h : b->dev) a.max_z = std::max(a.max_z, (int32_t)h->p.n_zones);
     a.work = b->work_ctr;
     a.t0 = b->t0;
     a.t0_mut = b->t0;

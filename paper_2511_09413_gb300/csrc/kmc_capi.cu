@@ -171,6 +171,7 @@ void fill_args(kmc_handle *h)
     a.P0site = h->P0site;
     a.P0f = h->P0f;
     a.P0bnd = h->P0bnd;
+    a.bgd = h->bgd;
     a.K = h->K;
     a.self = h->args_dev;
     a.J = h->J;
@@ -279,7 +280,8 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
     h->args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
     h->occ_init = (uint8_t *)h->alloc(occ_bytes);
     h->Jr = (int64_t *)h->alloc(sizeof(int64_t) * (size_t)R);
-    if (!h->Jr || !h->occ_init || !h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
+    h->bgd = (double2 *)h->alloc(sizeof(double2) * (size_t)R * (size_t)Z);
+    if (!h->bgd || !h->Jr || !h->occ_init || !h->args_dev || !h->occ || !h->V || !h->N0 || !h->K || !h->J || !h->Zc || !h->log || !h->misc)
         return fail(KMC_E_NOMEM, "device allocation failed");
     if (Ea) {
         h->P0site = (double *)h->alloc(sizeof(double) * (size_t)(R * L));
@@ -313,6 +315,7 @@ int create_impl(const kmc_params *params, const double *V, int64_t n_total, cons
     }
     unsigned long long *bad = h->misc + 5;
     CK(setup_row_counts(h->occ, h->stride, (int32_t)R, (int32_t)L, h->N0, bad, s), "row counts");
+    CK(setup_background(h->N0, (int32_t)R, (int32_t)L, (int32_t)Z, h->K, h->bgd, s), "background");
     CK(cudaMemcpyAsync(h->occ_init, h->occ, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
 
     int *p0bad = (int *)(h->misc + 6);
@@ -572,6 +575,8 @@ int kmc_step_n(kmc_handle *h, int64_t n_steps)
         h->args.n_steps = (int32_t)n;
         cudaError_t e = sweep_launch(h->args, h->launch, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+        e = zone_scan(h->Zc, h->t, (int)n, h->p.n_zones, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "zone-count scan launch");
         h->t += n;
         n_steps -= n;
     }

@@ -36,6 +36,7 @@ struct kmc_handle {
     double *P0site = nullptr;
     float *P0f = nullptr;
     float2 *P0bnd = nullptr;
+    double2 *bgd = nullptr;                   // [R][Z] backgrounds of the FP64 decision paths
     kmc::DevConst *K = nullptr;
     unsigned long long *J = nullptr;
     unsigned long long *Zc = nullptr;

@@ -24,6 +24,8 @@ struct DevConst {
     double kT;      // k_B T, k_B = 8.6173e-5 eV/K (Eq. 4)
     double d;       // hop distance
     double t_dev;   // L d
+    double xs;      // -d / (t_dev kT): dV -> the exponent of Eq. 4 (fast FP64 band)
+    double half_invL; // 0.5 / L
     float P0f, E_inf, E_outf, pad;
     int32_t status; // 0 ok, else a KMC_E_* code found while deriving
     int32_t pad2;
@@ -46,6 +48,7 @@ struct SweepArgs {
     const double *P0site;      // [R][L] or null
     const float *P0f;          // [R][L] P0site rounded to FP32, or null
     const float2 *P0bnd;       // [R][Z] (min, max) of P0site over the zone, or null
+    const double2 *bgd;        // [R][Z] (N0 w_z / L, D'_z) in FP64 for the FP64 paths, or null
     const DevConst *K;
     const SweepArgs *self;     // copy of these arguments in device memory (rare paths)
     unsigned long long *J;     // [n_steps_total] int64 two's complement
@@ -107,8 +110,10 @@ struct BatchArgs {
     const BatchItem *items;  // [n_items] in scheduling order
     int32_t n_items;
     int32_t n_steps;         // steps of this launch
-    int32_t flush;           // steps between trace flushes
-    int32_t pad;
+    int32_t flush;           // steps between flushes of the warps' counters
+    int32_t n_inst;          // devices
+    int32_t max_z;           // the largest zone count of the devices
+    int32_t pad2;
     unsigned *work;          // next work item (reset by the advance kernel)
     const int64_t *t0;       // absolute step of the launch's first step
     int64_t *t0_mut;         // the same counter, advanced after the launch
@@ -132,6 +137,8 @@ constexpr double kAcceptAutoP0 = 1.0 / 128.0;
 size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bool acc);
 int sweep_pick_lpr(int L, int *wpl);
 cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s);
+// zone-count trace of steps [t0, t0 + n): per-step changes -> counts (after a sweep)
+cudaError_t zone_scan(unsigned long long *Zc, int64_t t0, int n, int Z, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
 // gradient passes of a batch: one persistent launch over (device, tile) items
 // whose per-device arguments (b.inst) are gradient-pass arguments
@@ -161,6 +168,10 @@ cudaError_t setup_p0_bounds(const double *P0, int32_t R, int32_t L, int32_t Z, c
 cudaError_t setup_p0_float(const double *P0, int64_t n, float *out, cudaStream_t s);
 cudaError_t setup_row_counts(const uint8_t *occ, int64_t stride, int32_t R, int32_t L,
                              int32_t *N0, unsigned long long *bad, cudaStream_t s);
+// bgd[r][z] = (N0[r] w_z / L in the oracle's FP64 order, D'_z): the background
+// of zone z of rail r and its part of Q_z - Qbar (S2.1.8 reading)
+cudaError_t setup_background(const int32_t *N0, int32_t R, int32_t L, int32_t Z, const DevConst *K,
+                             double2 *bgd, cudaStream_t s);
 cudaError_t setup_init_bernoulli(const kmc_params &p, uint8_t *occ, int64_t stride,
                                  cudaStream_t s);
 // mode 0: count init keys <= key_bound; mode 1: keys == key_bound with linear index <= idx_bound

@@ -193,6 +193,7 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
     a.log_cap = kLogCap;
     a.counters = misc + 1;
     a.Jr = nullptr;     // no per-rail current on this path
+    a.bgd = nullptr;    // no background table: undecided draws take the exact path
     int bnd[KMC_MAX_ZONES + 1];
     for (int z = 0; z <= Z; ++z) bnd[z] = (int)(((int64_t)z * L) / Z);
     for (int z = 0; z <= KMC_MAX_ZONES; ++z) a.bnd[z] = z <= Z ? bnd[z] : L;
@@ -245,6 +246,8 @@ extern "C" int kmc_sweep_noalloc(const kmc_params *p, uint8_t *occ_dev, int64_t 
         const int64_t n = std::min<int64_t>(left, 1 << 30);
         a.n_steps = (int32_t)n;
         if ((e = sweep_launch(a, l, s)) != cudaSuccess) return cuda_fail(e, "sweep launch");
+        if ((e = zone_scan(a.Zc, a.t0, (int)n, Z, s)) != cudaSuccess)
+            return cuda_fail(e, "zone-count scan launch");
         a.t0 += n;
         left -= n;
     }

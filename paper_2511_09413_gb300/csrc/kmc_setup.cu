@@ -67,6 +67,8 @@ __global__ void constants_kernel(const kmc_params p, DevConst *K)
     c.ka = __dmul_rn(p.kappa, p.alpha_V);
     c.d = p.site_spacing_nm;
     c.t_dev = __dmul_rn((double)p.n_sites, p.site_spacing_nm);
+    c.xs = -(c.d / c.t_dev) / kT;
+    c.half_invL = 0.5 / (double)p.n_sites;
     c.P0f = (float)c.P0;
     c.E_inf = (float)c.E_in;
     c.E_outf = (float)c.E_out;
@@ -187,6 +189,29 @@ __global__ void exp_table_kernel(double cm, int32_t M, double *etL, double *etH,
     if (i < nH) etH[i] = exp(__dmul_rn(cm, (double)((int64_t)i * 1024 - M)));
 }
 
+// Background of each zone of each rail for the FP64 decision paths (one
+// thread per rail): c_z = N0 w_z / L, an exact product rounded once by the
+// division, as the exact path uses it, and D'_z = D_z - sum_z' w_z' D_z' / L
+// with D_z = sum_{z'<z} c_z' + c_z / 2, the background part of Q_z - Qbar
+// (S2.1.8 reading), so that Q_z - Qbar = (L (Pb_z + Pb_z+1) - F) / (2 L) - D'_z.
+__global__ void background_kernel(const int32_t *N0, int32_t R, int32_t L, int32_t Z,
+                                  const DevConst *K, double2 *bgd)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double run = 0.0, acc = 0.0;
+    for (int z = 0; z < Z; ++z) {
+        const int w = K->bnd[z + 1] - K->bnd[z];
+        const double c = __ddiv_rn(__dmul_rn((double)N0[r], (double)w), (double)L);
+        const double D = run + 0.5 * c;
+        run += c;
+        acc += (double)w * D;
+        bgd[r * Z + z] = make_double2(c, D);
+    }
+    const double mean = acc / (double)L;
+    for (int z = 0; z < Z; ++z) bgd[r * Z + z].y -= mean;
+}
+
 int grid_for(int64_t n, int block)
 {
     int64_t g = (n + block - 1) / block;
@@ -230,6 +255,13 @@ cudaError_t setup_exp_tables(double cm, int32_t M, double *etL, double *etH, int
 {
     const int n = nH > 1024 ? nH : 1024;
     exp_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(cm, M, etL, etH, nH);
+    return cudaGetLastError();
+}
+
+cudaError_t setup_background(const int32_t *N0, int32_t R, int32_t L, int32_t Z, const DevConst *K,
+                             double2 *bgd, cudaStream_t s)
+{
+    background_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(N0, R, L, Z, K, bgd);
     return cudaGetLastError();
 }
 

@@ -25,8 +25,11 @@
 //    rarely taken branch, and the exact FP64 path runs after the loop.
 //  * Moves are rare per step, so the move/conflict/apply phase runs only when
 //    the warp accepted at least one hop.
-//  * Per-step current and zone counts are reduced per CTA in shared memory and
-//    flushed to the int64 traces with one atomic per value every `flush` steps.
+//  * Per-step current and zone-count changes go straight to the int64 traces
+//    with one global reduction per warp and nonzero value (only steps that
+//    moved an ion have any); a prefix sum over the launch's steps
+//    (zone_scan_kernel) turns the zone-count changes into counts.  No CTA
+//    barrier: the warps of a CTA advance independently.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -238,7 +241,8 @@ struct WarpSmem {
 // Qbar, dV_z (S2.1.8), dE_z (Eq. 3), B_z (Eq. 4).  Every operation is an
 // explicitly rounded intrinsic so that no contraction changes the result.
 __device__ __forceinline__ void exact_zone(const int32_t *Pb, const DevConst *Kp, int Z, int L,
-                                        int32_t n0, double V, int zt, double *B, double *inv)
+                                        int32_t n0, const double2 *bgd, double V, int zt, double *B,
+                                        double *inv)
 {
     const DevConst &K = *Kp;
     const double Ld = (double)L;
@@ -246,7 +250,9 @@ __device__ __forceinline__ void exact_zone(const int32_t *Pb, const DevConst *Kp
     for (int z = 0; z < Z; ++z) {
         const int w = K.bnd[z + 1] - K.bnd[z];
         const int Nz = Pb[z + 1] - Pb[z];
-        const double C = __dsub_rn((double)Nz, __ddiv_rn(__dmul_rn((double)n0, (double)w), Ld));
+        // background N0 w_z / L: the rail's precomputed row when there is one
+        const double bz = bgd ? bgd[z].x : __ddiv_rn(__dmul_rn((double)n0, (double)w), Ld);
+        const double C = __dsub_rn((double)Nz, bz);
         const double Q = __dadd_rn(run, __dmul_rn(0.5, C));
         run = __dadd_rn(run, C);
         acc = __dadd_rn(acc, __dmul_rn((double)w, Q));
@@ -415,23 +421,61 @@ __device__ __forceinline__ bool slow_candidate(WarpSmem<LPR, WPL> S, const Sweep
     if (!undecided) return false;   // decided (and applied) in the draw loop
     const DevConst *K = g->K;
     const int L = g->L, Z = g->Z;
-    double B, inv;
-    exact_zone(S.Pb() + g2 * (Z + 1), K, Z, L, S.N0s()[g2], g->V[t], z, &B, &inv);
+    const double V = g->V[t];
     const double P0k = persite ? g->P0site[r2 * L + site] : K->P0;
+    const double baseR = D.kindR == 1 ? K->E_in : (D.kindR == 2 ? K->E_out : P0k);
+    const double baseL = D.kindL == 1 ? K->E_in : (D.kindL == 2 ? K->E_out : P0k);
+    const uint64_t wR = ((uint64_t)x.y << 32) | x.x, wL = ((uint64_t)x.w << 32) | x.z;
     unsigned ne = 0;
-    if (D.dR == 2) {
-        const double base = D.kindR == 1 ? K->E_in : (D.kindR == 2 ? K->E_out : P0k);
-        const double p = __dmul_rn(__dmul_rn(base, inv), B);       // Eq. 6
-        D.dR = exact_trial(((uint64_t)x.y << 32) | x.x, p, g->log, g->log_count, g->log_cap,
-                           (int32_t)rg, t, site, 0, D.kindR) ? 1 : 0;
-        ++ne;
+    // FP64 band: p from Q_z - Qbar = m_z / (2 L) - D'_z (integer m_z, the rail's
+    // D'_z) in a dozen FP64 operations.  Its relative error is below 1e-13 for
+    // every exponent |x| < 600 (a few roundings of x, each moving p by at most
+    // |x| ulp), so a draw more than 1e-11 from it has the exact p on the same
+    // side and is not a near-threshold decision (|u - p| > 1e-12).  Only draws
+    // within 1e-11 take the exact path below.
+    if (g->bgd) {
+        const int32_t *Pb = S.Pb() + g2 * (Z + 1);
+        const int m = L * (Pb[z] + Pb[z + 1]) - S.Fs()[g2];
+        const double dq = __fma_rn((double)m, K->half_invL, -g->bgd[r2 * Z + z].y);
+        const double xx = __dmul_rn(__fma_rn(-K->ka, dq, V), K->xs);
+        if (fabs(xx) < 600.0) {
+            const double Bf = exp(xx);
+            const double invf = 1.0 / (1.0 + Bf);
+            if (D.dR == 2) {
+                const double d = __dsub_rn(__dmul_rn((double)(wR >> 11), 0x1.0p-53),
+                                           __dmul_rn(__dmul_rn(baseR, invf), Bf));
+                if (fabs(d) > 1e-11) {
+                    D.dR = d <= 0.0 ? 1 : 0;
+                    ++ne;
+                }
+            }
+            if (D.dL == 2) {
+                const double d = __dsub_rn(__dmul_rn((double)(wL >> 11), 0x1.0p-53),
+                                           __dmul_rn(baseL, invf));
+                if (fabs(d) > 1e-11) {
+                    D.dL = d <= 0.0 ? 1 : 0;
+                    ++ne;
+                }
+            }
+        }
     }
-    if (D.dL == 2) {
-        const double base = D.kindL == 1 ? K->E_in : (D.kindL == 2 ? K->E_out : P0k);
-        const double p = __dmul_rn(base, inv);                      // Eq. 5
-        D.dL = exact_trial(((uint64_t)x.w << 32) | x.z, p, g->log, g->log_count, g->log_cap,
-                           (int32_t)rg, t, site, 1, D.kindL) ? 1 : 0;
-        ++ne;
+    if (D.dR == 2 || D.dL == 2) {
+        // exact path: p in FP64 with the oracle's operation order, u <= p
+        double B, inv;
+        exact_zone(S.Pb() + g2 * (Z + 1), K, Z, L, S.N0s()[g2], g->bgd ? g->bgd + r2 * Z : nullptr,
+                   V, z, &B, &inv);
+        if (D.dR == 2) {
+            const double p = __dmul_rn(__dmul_rn(baseR, inv), B);   // Eq. 6
+            D.dR = exact_trial(wR, p, g->log, g->log_count, g->log_cap, (int32_t)rg, t, site, 0,
+                               D.kindR) ? 1 : 0;
+            ++ne;
+        }
+        if (D.dL == 2) {
+            const double p = __dmul_rn(baseL, inv);                  // Eq. 5
+            D.dL = exact_trial(wL, p, g->log, g->log_count, g->log_cap, (int32_t)rg, t, site, 1,
+                               D.kindL) ? 1 : 0;
+            ++ne;
+        }
     }
     atomicAdd(&g->counters[1], (unsigned long long)ne);
     return record_move<LPR, WPL, GRAD>(S, D, g2);
@@ -693,12 +737,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
     S.npo = (uint32_t)(Ly::FIXED + S.rz + 2 * S.gz + Ly::pb_only(Z));
     S.goff = (uint32_t)wb0;
     S.gzq = (uint32_t)align16((size_t)8 * G * Z);
-    // the gradient pass writes no traces: no trace buffer
-    const int trace_len = GRAD ? 0 : flush * (1 + Z);
-    int32_t *trace = (int32_t *)(smem + (size_t)nwarps * wb);
-    // the CTA's running count of each zone, carried from flush to flush
-    int32_t *zrun = trace + trace_len;
-    uint8_t *zone_tab = (uint8_t *)(zrun + (GRAD ? 0 : align16((size_t)4 * Z) / 4));
+    uint8_t *zone_tab = smem + (size_t)nwarps * wb;
 
     // ---- per-CTA tables and per-warp staging
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -706,8 +745,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         while (a.bnd[z + 1] <= k) ++z;
         zone_tab[k] = (uint8_t)z;
     }
-    for (int i = threadIdx.x; i < trace_len; i += blockDim.x) trace[i] = 0;
-    if (!GRAD && (int)threadIdx.x < Z) zrun[threadIdx.x] = 0;
     for (int pi = lane; pi < G * Z; pi += 32) S.Np()[pi] = 0;
     if (lane == 0) {
         S.cnt()[0] = 0;
@@ -820,7 +857,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
         const int c1 = min(n_steps, c0 + flush);
         for (int s = c0; s < c1; ++s) {
             const uint32_t t = (uint32_t)(t0 + s);
-            int32_t *tr = trace + (s - c0) * (1 + Z);
 
             // the brick-wall rule's active bonds alternate: its candidates change
             // every step even when the occupancy does not
@@ -1049,8 +1085,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             }
 
             // ---- zone counts of the step-start occupancy into the trace, as
-            //      changes: they can only change when the occupancy was rebuilt,
-            //      and the flush sums them over the steps of the chunk
+            //      changes (the launch's first step: the counts themselves):
+            //      they can only change when the occupancy was rebuilt, and a
+            //      prefix sum over the launch's steps (zone_scan) turns them
+            //      into counts
             if constexpr (!GRAD) {
                 if (rebuilt) {
                     for (int pi = lane; pi < G * Z; pi += 32) {
@@ -1059,7 +1097,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                         const int nz = S.Pb()[g2 * (Z + 1) + z + 1] - S.Pb()[g2 * (Z + 1) + z];
                         const int dz = nz - S.Np()[pi];
                         if (dz != 0) {
-                            atomicAdd(&tr[1 + z], dz);
+                            atomicAdd(&a.Zc[(t0 + s) * Z + z], (unsigned long long)(long long)dz);
                             S.Np()[pi] = nz;
                         }
                     }
@@ -1294,7 +1332,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                     Jrail = v;
                 } else {
                     const int Jw = __reduce_add_sync(FULL, Jl);
-                    if (lane == 0 && Jw != 0) atomicAdd(&tr[0], Jw);
+                    if (lane == 0 && Jw != 0)
+                        atomicAdd(&a.J[t0 + s], (unsigned long long)(long long)Jw);
                     // per-rail current: the rail's own sum (the warp's when G == 1)
                     if (a.Jr) {
                         if (G == 1) {
@@ -1325,26 +1364,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             }
             __syncwarp();
         }
-        // ---- flush this chunk's traces and counters
+        // ---- flush this warp's counters and per-rail current (no CTA barrier:
+        //      warps advance independently through the launch)
         if constexpr (GRAD) continue;
-        __syncthreads();
-        for (int i = threadIdx.x; i < c1 - c0; i += blockDim.x) {
-            const int v = trace[i * (1 + Z)];
-            if (v != 0) atomicAdd(&a.J[t0 + c0 + i], (unsigned long long)(long long)v);
-            trace[i * (1 + Z)] = 0;
-        }
-        if ((int)threadIdx.x < Z) {
-            // thread z carries the CTA's count of zone z from chunk to chunk
-            const int z = threadIdx.x;
-            int run = zrun[z];
-            for (int i = 0; i < c1 - c0; ++i) {
-                run += trace[i * (1 + Z) + 1 + z];
-                trace[i * (1 + Z) + 1 + z] = 0;
-                if (run != 0)
-                    atomicAdd(&a.Zc[(t0 + c0 + i) * Z + z], (unsigned long long)(long long)run);
-            }
-            zrun[z] = run;
-        }
         if (lane == 0) {
             const uint32_t nd = S.cnt()[0], nmv = S.cnt()[1];
             if (nd) atomicAdd(&a.counters[0], (unsigned long long)nd);
@@ -1359,7 +1381,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
             if (v != 0) a.Jr[rail] += v;
             S.jr()[seg] = 0;
         }
-        __syncthreads();
+        __syncwarp();
     }
 
     if constexpr (GRAD) {
@@ -1560,6 +1582,57 @@ __global__ void __launch_bounds__(256, 2) sweep_batch_grad_kernel(const BatchArg
     }
 }
 
+// Zone-count traces of steps [t0, t0 + n): the sweep leaves there, for every
+// step, the change of each zone's count (the first step: the counts), and an
+// inclusive prefix sum over the steps turns them into counts.  One block per
+// zone (blockIdx.x), 1,024 steps per pass.
+__device__ __forceinline__ void scan_zone_trace(unsigned long long *Zc, int64_t t0, int n, int Z,
+                                                int z)
+{
+    __shared__ long long part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        long long v = i < n ? (long long)Zc[(t0 + i) * Z + z] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long u = __shfl_up_sync(FULL, v, off);
+            if (lane >= off) v += u;
+        }
+        if (lane == 31) part[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = part[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long u = __shfl_up_sync(FULL, w, off);
+                if (lane >= off) w += u;
+            }
+            part[lane] = w;
+        }
+        __syncthreads();
+        if (warp > 0) v += part[warp - 1];
+        if (i < n) Zc[(t0 + i) * Z + z] = (unsigned long long)(v + carry);
+        carry += part[31];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) zone_scan_kernel(unsigned long long *Zc, int64_t t0, int n,
+                                                         int Z)
+{
+    scan_zone_trace(Zc, t0, n, Z, blockIdx.x);
+}
+
+// The same for every device of a batch after a launch (grid: max Z x devices).
+__global__ void __launch_bounds__(1024) batch_zone_scan_kernel(const BatchArgs b)
+{
+    const SweepArgs &ia = b.inst[blockIdx.y];
+    if ((int)blockIdx.x >= ia.Z || ia.Zc == nullptr) return;
+    scan_zone_trace(ia.Zc, *b.t0, b.n_steps, ia.Z, blockIdx.x);
+}
+
 // Advance the batch's step counter and re-arm its work counter.
 __global__ void batch_advance_kernel(int64_t *t0, unsigned *work, int n_steps)
 {
@@ -1634,8 +1707,8 @@ size_t sweep_smem_bytes(int lpr, int wpl, int Z, int L, int warps, int flush, bo
     else if (lpr == 8) wb = Layout<8, 1>::bytes(Z, acc);
     else if (lpr == 16) wb = Layout<16, 1>::bytes(Z, acc);
     else wb = Layout<32, 1>::bytes(Z, acc);
-    return (size_t)warps * wb + align16(sizeof(int32_t) * flush * (1 + Z)) +
-           align16(sizeof(int32_t) * (size_t)Z) + align16((size_t)L);
+    (void)flush;   // the flush interval no longer needs shared memory
+    return (size_t)warps * wb + align16((size_t)L);
 }
 
 size_t grad_smem_bytes(int lpr, int wpl, int Z, int L, int warps)
@@ -1745,7 +1818,16 @@ cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, b
     else sweep_batch_kernel<false><<<grid, warps * 32, smem, s>>>(b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    batch_zone_scan_kernel<<<dim3(b.max_z, b.n_inst), 1024, 0, s>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     batch_advance_kernel<<<1, 32, 0, s>>>(b.t0_mut, b.work, b.n_steps);
+    return cudaGetLastError();
+}
+
+cudaError_t zone_scan(unsigned long long *Zc, int64_t t0, int n, int Z, cudaStream_t s)
+{
+    zone_scan_kernel<<<Z, 1024, 0, s>>>(Zc, t0, n, Z);
     return cudaGetLastError();
 }
 
