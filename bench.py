@@ -377,9 +377,10 @@ def run_kmc(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": args.steps,
                     "h2d_bytes_per_step": int(Vpin.nbytes),
                     "d2h_bytes_per_step": int(Jpin.nbytes + Zpin.nbytes)},
-            "gpu_launches": args.steps,
+            # per timed step: one sweep_kernel launch and one zone_scan_kernel launch
+            "gpu_launches": 2 * args.steps,
             "counters": {"philox_blocks_per_site_update": draws / su_per_step,
-                         "exact_fp64_decisions": int(cnt1[1] - cnt0[1]),
+                         "fp64_decisions": int(cnt1[1] - cnt0[1]),
                          "moves": int(cnt1[2] - cnt0[2])},
             "wall_s": wall,
         }
