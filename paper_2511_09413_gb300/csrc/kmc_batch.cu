@@ -27,8 +27,8 @@ struct kmc_batch {
     int64_t t = 0;                       // current absolute step
     int64_t n_total = 0;
     SweepArgs *inst = nullptr;           // device copies of the handles' arguments
-    BatchItem *items = nullptr;
-    unsigned *work_ctr = nullptr;
+    BatchItem *items = nullptr;          // grouped by kernel shape, longest tiles first in each
+    unsigned *work_ctr = nullptr;        // [kShapeKinds] next work item of each shape
     int64_t *t0 = nullptr;
     int n_items = 0;
     int warps = 8;
@@ -36,8 +36,8 @@ struct kmc_batch {
     int flush = 256;
     int acc_req = -1;                    // accept path: -1 automatic, 0 off, 1 on
     int acc = 0;                         // accept path in effect
-    size_t smem = 0;
-    int grid = 0;
+    BatchPlan plan{};                    // CTAs and shared memory of each shape's launch
+    int cls_off[kShapeKinds + 1] = {};   // items of shape k: [cls_off[k], cls_off[k + 1])
     uint32_t rk0[10], rk1[10];
     cudaGraphExec_t graph = nullptr;     // one launch of steps_per_launch steps + advance
     int graph_warps = 0, graph_steps = 0, graph_acc = -1;
@@ -73,45 +73,72 @@ void drop_graph(kmc_batch *b)
 
 // Work list for a CTA size: one item per tile of 32/LPR * warps rails, larger
 // tiles (longer rails) first so that the dynamic schedule ends evenly.
-int build_items(kmc_batch *b, int warps)
+// Work items of a list of devices: every device's rails cut into tiles of
+// (32 / lanes per rail) x warps rails, grouped by kernel shape and, within a
+// shape, longest tiles first.  Returns the items and the shape offsets.
+void make_items(const std::vector<const kmc_params *> &devs, const std::vector<int> &inst, int warps,
+                std::vector<BatchItem> &sorted, int *cls_off)
 {
-    if (b->work) cudaStreamSynchronize(b->work);   // launches in flight may read the old list
     std::vector<BatchItem> items;
     std::vector<int64_t> cost;
-    size_t smem = 0;
-    int dev = 0, max_smem = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (max_smem <= 0) max_smem = 48 * 1024;
-    max_smem = std::min(max_smem, 200 * 1024);
-    float p0max = 0.0f;
-    for (const kmc_handle *h : b->dev) p0max = std::max(p0max, h->args.P0f_scalar);
-    const int acc = b->acc_req >= 0 ? b->acc_req : (p0max >= kAcceptAutoP0 ? 1 : 0);
-    for (size_t i = 0; i < b->dev.size(); ++i) {
-        const kmc_params &p = b->dev[i]->p;
+    for (size_t i = 0; i < devs.size(); ++i) {
+        const kmc_params &p = *devs[i];
         int wpl = 1;
         const int lpr = sweep_pick_lpr(p.n_sites, &wpl);
-        const int G = 32 / lpr;
-        const int64_t tile = (int64_t)G * warps;
-        smem = std::max(smem, sweep_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, warps, b->flush,
-                                               acc != 0));
+        const int64_t tile = (int64_t)(32 / lpr) * warps;
         for (int64_t r0 = 0; r0 < p.n_rails; r0 += tile) {
             BatchItem it;
-            it.inst = (int32_t)i;
+            it.inst = inst[i];
             it.kind = sweep_kind(lpr, wpl);
             it.tile_rail0 = r0;
             items.push_back(it);
             cost.push_back(std::min<int64_t>(tile, p.n_rails - r0) * p.n_sites);
         }
     }
-    if (smem + 1024 > (size_t)max_smem)
-        return fail(KMC_E_ARG, "batch: shared memory for this CTA size exceeds the device limit");
     std::vector<size_t> order(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-    std::vector<BatchItem> sorted(items.size());
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        return items[x].kind != items[y].kind ? items[x].kind < items[y].kind : cost[x] > cost[y];
+    });
+    sorted.resize(items.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    for (int k = 0; k <= kShapeKinds; ++k) cls_off[k] = 0;
+    for (const BatchItem &it : sorted) ++cls_off[it.kind + 1];
+    for (int k = 0; k < kShapeKinds; ++k) cls_off[k + 1] += cls_off[k];
+}
+
+int build_items(kmc_batch *b, int warps)
+{
+    if (b->work) cudaStreamSynchronize(b->work);   // launches in flight may read the old list
+    int dev = 0, max_smem = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (max_smem <= 0) max_smem = 48 * 1024;
+    max_smem = std::min(max_smem, 200 * 1024);
+    float p0max = 0.0f;
+    for (const kmc_handle *h : b->dev) p0max = std::max(p0max, h->args.P0f_scalar);
+    const int acc = b->acc_req >= 0 ? b->acc_req : (p0max >= kAcceptAutoP0 ? 1 : 0);
+    // shared memory of each shape's CTAs: the largest of its devices' tiles
+    BatchPlan plan{};
+    std::vector<const kmc_params *> devs;
+    std::vector<int> inst;
+    for (size_t i = 0; i < b->dev.size(); ++i) {
+        const kmc_params &p = b->dev[i]->p;
+        int wpl = 1;
+        const int lpr = sweep_pick_lpr(p.n_sites, &wpl);
+        const int k = sweep_kind(lpr, wpl);
+        plan.smem[k] = std::max(plan.smem[k], sweep_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, warps,
+                                                               b->flush, acc != 0));
+        devs.push_back(&p);
+        inst.push_back((int)i);
+    }
+    for (int k = 0; k < kShapeKinds; ++k)
+        if (plan.smem[k] + 1024 > (size_t)max_smem)
+            return fail(KMC_E_ARG, "batch: shared memory for this CTA size exceeds the device limit");
+    std::vector<BatchItem> sorted;
+    int cls_off[kShapeKinds + 1];
+    make_items(devs, inst, warps, sorted, cls_off);
     if (b->items) cudaFreeAsync(b->items, b->user);
     b->items = nullptr;
     BCK(cudaMallocAsync((void **)&b->items, sizeof(BatchItem) * std::max<size_t>(1, sorted.size()),
@@ -122,14 +149,17 @@ int build_items(kmc_batch *b, int warps)
         "copy items");
     BCK(cudaStreamSynchronize(b->user), "batch items");
     b->n_items = (int)sorted.size();
-    b->smem = smem;
     b->warps = warps;
     b->acc = acc;
-    // persistent grid: every SM full (3 CTAs of 8 warps, or more smaller ones)
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = std::max(1, 24 / warps);
-    b->grid = std::max(1, std::min(b->n_items, sms * per_sm));
+    // one persistent grid per shape: every SM full (as many CTAs as its
+    // registers and shared memory allow), at most one CTA per item
+    for (int k = 0; k < kShapeKinds; ++k) {
+        const int n = cls_off[k + 1] - cls_off[k];
+        b->cls_off[k] = cls_off[k];
+        plan.grid[k] = n > 0 ? std::min(n, sms * batch_ctas_per_sm(k, acc, warps, plan.smem[k])) : 0;
+    }
+    b->cls_off[kShapeKinds] = cls_off[kShapeKinds];
+    b->plan = plan;
     drop_graph(b);
     return KMC_OK;
 }
@@ -141,6 +171,7 @@ BatchArgs batch_args(const kmc_batch *b, int n_steps)
     a.inst = b->inst;
     a.items = b->items;
     a.n_items = b->n_items;
+    for (int k = 0; k <= kShapeKinds; ++k) a.cls_off[k] = b->cls_off[k];
     a.n_steps = n_steps;
     a.flush = b->flush;
     a.n_inst = (int32_t)b->dev.size();
@@ -166,8 +197,8 @@ int run_chunk(kmc_batch *b, int n_steps)
             drop_graph(b);
             cudaGraph_t g = nullptr;
             BCK(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal), "begin capture");
-            cudaError_t le = batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem,
-                                          b->acc != 0, b->work);
+            cudaError_t le = batch_launch(batch_args(b, n_steps), b->plan, b->warps, b->acc != 0,
+                                          b->work);
             cudaError_t ce = cudaStreamEndCapture(b->work, &g);
             if (le != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -184,7 +215,7 @@ int run_chunk(kmc_batch *b, int n_steps)
         BCK(cudaGraphLaunch(b->graph, b->work), "cudaGraphLaunch");
         return KMC_OK;
     }
-    BCK(batch_launch(batch_args(b, n_steps), b->grid, b->warps, b->smem, b->acc != 0, b->work),
+    BCK(batch_launch(batch_args(b, n_steps), b->plan, b->warps, b->acc != 0, b->work),
         "batched launch");
     return KMC_OK;
 }
@@ -256,12 +287,12 @@ int kmc_batch_create(const kmc_params *params, int32_t n_inst, const double *con
     std::vector<SweepArgs> host(n_inst);
     for (int i = 0; i < n_inst; ++i) host[i] = b->dev[i]->args;
     if ((e = cudaMallocAsync((void **)&b->inst, sizeof(SweepArgs) * n_inst, b->user)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&b->work_ctr, sizeof(unsigned) * 4, b->user)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&b->work_ctr, sizeof(unsigned) * kShapeKinds, b->user)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&b->t0, sizeof(int64_t) * 2, b->user)) != cudaSuccess)
         return bail(cuda_fail(e, "batch allocation"));
     if ((e = cudaMemcpyAsync(b->inst, host.data(), sizeof(SweepArgs) * n_inst, cudaMemcpyHostToDevice,
                              b->user)) != cudaSuccess ||
-        (e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned) * 4, b->user)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned) * kShapeKinds, b->user)) != cudaSuccess ||
         (e = cudaMemsetAsync(b->t0, 0, sizeof(int64_t) * 2, b->user)) != cudaSuccess)
         return bail(cuda_fail(e, "batch set-up"));
     rc = build_items(b, b->warps);
@@ -484,32 +515,30 @@ int kmc_batch_grad_all(kmc_batch *b, const double *const *dLoss_dJ, const double
             return m;
         };
         while (warps > 1 && smem_for(warps) > (size_t)max_smem) warps >>= 1;
-        const size_t smem = smem_for(warps);
-        if (smem > (size_t)max_smem)
+        if (smem_for(warps) > (size_t)max_smem)
             return fail(KMC_E_ARG, "batched gradient pass: shared memory exceeds the device limit");
-        // work items, longest tiles first
-        std::vector<BatchItem> items;
-        std::vector<int64_t> cost;
+        // work items grouped by shape, longest tiles first in each; one
+        // persistent launch per shape, its shared memory the largest tile's
+        std::vector<const kmc_params *> devs;
+        std::vector<int> inst;
+        BatchPlan plan{};
         for (int i = 0; i < n_inst; ++i) {
             if (!active[(size_t)i]) continue;
             const kmc_params &p = b->dev[(size_t)i]->p;
             int wpl = 1;
             const int lpr = sweep_pick_lpr(p.n_sites, &wpl);
-            const int64_t tile = (int64_t)(32 / lpr) * warps;
-            for (int64_t r0 = 0; r0 < p.n_rails; r0 += tile) {
-                BatchItem it;
-                it.inst = i;
-                it.kind = sweep_kind(lpr, wpl);
-                it.tile_rail0 = r0;
-                items.push_back(it);
-                cost.push_back(std::min<int64_t>(tile, p.n_rails - r0) * p.n_sites);
-            }
+            const int k = sweep_kind(lpr, wpl);
+            plan.smem[k] = std::max(plan.smem[k], grad_smem_bytes(lpr, wpl, p.n_zones, p.n_sites, warps));
+            devs.push_back(&p);
+            inst.push_back(i);
         }
-        std::vector<size_t> order(items.size());
-        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-        std::vector<BatchItem> sorted(items.size());
-        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        std::vector<BatchItem> sorted;
+        int cls_off[kShapeKinds + 1];
+        make_items(devs, inst, warps, sorted, cls_off);
+        for (int k = 0; k < kShapeKinds; ++k) {
+            const int n = cls_off[k + 1] - cls_off[k];
+            plan.grid[k] = n > 0 ? std::min(n, sms * batch_ctas_per_sm(k, 2, warps, plan.smem[k])) : 0;
+        }
         SweepArgs *ginst = nullptr;
         BatchItem *gitems = nullptr;
         BCK(cudaMallocAsync((void **)&ginst, sizeof(SweepArgs) * (size_t)n_inst, b->user), "grad args");
@@ -522,14 +551,15 @@ int kmc_batch_grad_all(kmc_batch *b, const double *const *dLoss_dJ, const double
         a.inst = ginst;
         a.items = gitems;
         a.n_items = (int)sorted.size();
-        const int grid = std::max(1, std::min(a.n_items, sms * 2 * std::max(1, 8 / warps)));
+        for (int k = 0; k <= kShapeKinds; ++k) a.cls_off[k] = cls_off[k];
         if ((e = cudaMemcpyAsync(ginst, gargs.data(), sizeof(SweepArgs) * (size_t)n_inst,
                                  cudaMemcpyHostToDevice, b->user)) == cudaSuccess &&
             (e = cudaMemcpyAsync(gitems, sorted.data(), sizeof(BatchItem) * sorted.size(),
                                  cudaMemcpyHostToDevice, b->user)) == cudaSuccess &&
-            (e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned), b->user)) == cudaSuccess &&
-            (e = batch_grad_launch(a, grid, warps, smem, b->user)) == cudaSuccess)
-            e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned), b->user);   // re-arm for the forward
+            (e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned) * kShapeKinds, b->user)) == cudaSuccess &&
+            (e = batch_grad_launch(a, plan, warps, b->user)) == cudaSuccess)
+            // re-arm for the forward
+            e = cudaMemsetAsync(b->work_ctr, 0, sizeof(unsigned) * kShapeKinds, b->user);
         cudaFreeAsync(gitems, b->user);
         cudaFreeAsync(ginst, b->user);
         if (e != cudaSuccess) return cuda_fail(e, "batched gradient pass");

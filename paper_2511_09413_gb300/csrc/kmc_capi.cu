@@ -380,10 +380,11 @@ int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss
         h->g_fJab = (double *)h->alloc(sizeof(double) * 2 * nt);
         h->g_fZa = (double *)h->alloc(sizeof(double) * nt * (size_t)Z);
         h->g_fZb = (double *)h->alloc(sizeof(double) * nt);
+        h->g_fZr = (int32_t *)h->alloc(sizeof(int32_t) * nt);
         h->g_out = (double *)h->alloc(sizeof(double) * 8);
         h->g_misc = (unsigned long long *)h->alloc(sizeof(unsigned long long) * 8);
         h->g_args_dev = (SweepArgs *)h->alloc(sizeof(SweepArgs));
-        if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_fJab || !h->g_fZa || !h->g_fZb ||
+        if (!h->g_occ || !h->g_state || !h->g_wJ || !h->g_fJab || !h->g_fZa || !h->g_fZb || !h->g_fZr ||
             !h->g_out || !h->g_misc || !h->g_args_dev)
             return fail(KMC_E_NOMEM, "device allocation failed (gradient pass)");
     }
@@ -409,6 +410,7 @@ int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss
     const double loo = R > 1 ? (double)(R - 1) : 0.0;
     const double scale = R > 1 ? (double)R / loo : 1.0;
     std::vector<double> fJab, fZa, fZb;
+    std::vector<int32_t> fZr;
     if (dLoss_dJ) {
         fJab.resize((size_t)(2 * n));
         for (int64_t i = 0; i < n; ++i) {
@@ -424,18 +426,31 @@ int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss
     if (dLoss_dZc) {
         fZa.resize((size_t)(n * Z));
         fZb.assign((size_t)n, 0.0);
-        for (int64_t i = 0; i < n; ++i)
+        fZr.assign((size_t)n, 0);
+        for (int64_t i = 0; i < n; ++i) {
+            int lo = (int)Z, hi = 0;
             for (int64_t z = 0; z < Z; ++z) {
                 const double w = dLoss_dZc[i * Z + z];
                 fZa[(size_t)(i * Z + z)] = w * scale;
                 if (loo > 0.0) fZb[(size_t)i] += w * ((double)Zt[(size_t)(i * Z + z)] / loo);
+                if (w != 0.0) {
+                    lo = std::min(lo, (int)z);
+                    hi = (int)z + 1;
+                }
             }
+            // the replay skips the zones outside [lo, hi), and the whole step
+            // when no weight is set (its share is then zero)
+            if (hi > 0) fZr[(size_t)i] = lo | (hi << 8);
+        }
         CK(cudaMemcpyAsync(h->g_fZa, fZa.data(), sizeof(double) * (size_t)(n * Z),
                            cudaMemcpyHostToDevice, s),
            "copy fZ coefficients");
         CK(cudaMemcpyAsync(h->g_fZb, fZb.data(), sizeof(double) * (size_t)n,
                            cudaMemcpyHostToDevice, s),
            "copy fZ offsets");
+        CK(cudaMemcpyAsync(h->g_fZr, fZr.data(), sizeof(int32_t) * (size_t)n,
+                           cudaMemcpyHostToDevice, s),
+           "copy fZ zone ranges");
     }
     CK(cudaMemcpyAsync(h->g_occ, h->occ_init, occ_bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
     CK(cudaMemsetAsync(h->g_state, 0, sizeof(double) * kGradState * (size_t)std::max<int64_t>(R, 1), s),
@@ -456,6 +471,7 @@ int kmc::grad_prepare(kmc_handle *h, const double *dLoss_dJ, const double *dLoss
     ga.fJab = dLoss_dJ ? (const double2 *)h->g_fJab : nullptr;
     ga.fZa = dLoss_dZc ? h->g_fZa : nullptr;
     ga.fZb = dLoss_dZc ? h->g_fZb : nullptr;
+    ga.fZr = dLoss_dZc ? h->g_fZr : nullptr;
     ga.gstate = h->g_state;
     ga.alpha = p.alpha_V;
     const double kT = 8.6173e-5 * p.T_K;

@@ -53,6 +53,7 @@ struct kmc_handle {
     double *g_wJ = nullptr;                   // weight of J_t per step
     double *g_fJab = nullptr;                 // per step (aJ, bJ): baselined current share
     double *g_fZa = nullptr, *g_fZb = nullptr;  // per step aZ[Z], bZ: baselined zone share
+    int32_t *g_fZr = nullptr;                   // per step range of zones with a nonzero aZ
     double *g_out = nullptr;                  // [8] sums and standard errors
     unsigned long long *g_misc = nullptr;     // log count and counters of the replay
     kmc::SweepArgs *g_args_dev = nullptr;

@@ -79,6 +79,8 @@ struct SweepArgs {
     const double2 *fJab;                 // [n_steps_total] (aJ, bJ)
     const double *fZa;                   // [n_steps_total][Z] aZ, or null
     const double *fZb;                   // [n_steps_total] bZ
+    const int32_t *fZr;                  // [n_steps_total] zones [lo, hi) that hold every
+                                         // nonzero aZ of the step, as lo | hi << 8 (0: none)
     double *gstate;                      // [R][kGradState] per-rail accumulators
     double alpha;                        // space-charge volts per excess ion
     double tdev_kT;                      // t_dev kB T (d ln B / d kappa denominator)
@@ -100,21 +102,38 @@ constexpr int kGradState = 5;
 // One work item of a batched launch: a tile of rails of one device.
 struct BatchItem {
     int32_t inst;        // device index in the batch
-    int32_t kind;        // kernel shape (sweep_kind of the device's lanes per rail)
+    int32_t kind;        // kernel shape (shape_kind of the device's lanes per rail)
     int64_t tile_rail0;  // first rail of the tile
+};
+
+// Kernel shapes of the tile body: lanes per rail 1, 2, 4, 8, 16, 32 with one
+// 32-bit word per lane (kinds 0-5), and 32 lanes of two words (kind 6).
+constexpr int kShapeKinds = 7;
+__host__ __device__ constexpr int shape_kind(int lpr, int wpl)
+{
+    return wpl == 2 ? 6 : lpr == 1 ? 0 : lpr == 2 ? 1 : lpr == 4 ? 2 : lpr == 8 ? 3 : lpr == 16 ? 4 : 5;
+}
+
+// Per-shape launches of a batch: CTAs and dynamic shared memory of each
+// shape's persistent launch (grid 0: the batch has no items of that shape).
+struct BatchPlan {
+    int grid[kShapeKinds];
+    size_t smem[kShapeKinds];
 };
 
 // Arguments of one batched launch.
 struct BatchArgs {
     const SweepArgs *inst;   // [n_inst] per-device arguments (device memory)
-    const BatchItem *items;  // [n_items] in scheduling order
+    const BatchItem *items;  // [n_items] grouped by shape, longest tiles first in each
+    int32_t cls_off[kShapeKinds + 1];  // items of shape k: [cls_off[k], cls_off[k + 1])
     int32_t n_items;
     int32_t n_steps;         // steps of this launch
     int32_t flush;           // steps between flushes of the warps' counters
     int32_t n_inst;          // devices
     int32_t max_z;           // the largest zone count of the devices
     int32_t pad2;
-    unsigned *work;          // next work item (reset by the advance kernel)
+    unsigned *work;          // [kShapeKinds] next work item of each shape (reset by the
+                             // advance kernel)
     const int64_t *t0;       // absolute step of the launch's first step
     int64_t *t0_mut;         // the same counter, advanced after the launch
     uint32_t rk0[10], rk1[10];
@@ -140,9 +159,13 @@ cudaError_t sweep_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t 
 // zone-count trace of steps [t0, t0 + n): per-step changes -> counts (after a sweep)
 cudaError_t zone_scan(unsigned long long *Zc, int64_t t0, int n, int Z, cudaStream_t s);
 cudaError_t sweep_set_smem_limits();
-// gradient passes of a batch: one persistent launch over (device, tile) items
-// whose per-device arguments (b.inst) are gradient-pass arguments
-cudaError_t batch_grad_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s);
+// gradient passes of a batch: one persistent launch per shape over its
+// (device, tile) items, whose per-device arguments (b.inst) are gradient-pass
+// arguments
+cudaError_t batch_grad_launch(const BatchArgs &b, const BatchPlan &plan, int warps, cudaStream_t s);
+// resident CTAs per SM of a shape's batched kernel (mode 0 forward, 1 forward
+// with the accept path, 2 gradient pass) at this CTA size and shared memory
+int batch_ctas_per_sm(int kind, int mode, int warps, size_t smem);
 // Philox-only probe: grid CTAs of 256 threads, each thread 4 x iters blocks
 cudaError_t philox_probe(int grid, int iters, uint32_t *sink, cudaStream_t s);
 // gradient pass: shared memory of a launch, the launch, and the final sum
@@ -152,8 +175,9 @@ cudaError_t grad_reduce(const double *gstate, int64_t R, const int32_t *N0, int 
                         int has_rho, double cEa, double cnu, double *out, cudaStream_t s);
 int sweep_kind(int lpr, int wpl);
 cudaError_t batch_set_smem_limit();
-// launches the batched sweep and then advances *t0 by n_steps and re-arms work
-cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, bool acc,
+// launches the batched sweep (one launch per shape), the zone-count scans, and
+// then advances *t0 by n_steps and re-arms the work counters
+cudaError_t batch_launch(const BatchArgs &b, const BatchPlan &plan, int warps, bool acc,
                          cudaStream_t s);
 
 // Sets the message returned by kmc_last_error() on this thread (kmc_capi.cu).

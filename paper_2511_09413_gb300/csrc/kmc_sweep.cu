@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <type_traits>
 
 #include "kmc_internal.h"
 
@@ -490,6 +491,28 @@ __device__ __forceinline__ double trial_weight(int A, int n, double r1, double q
 {
     return __fma_rn(-(double)n, q, __dmul_rn((double)A, r1));
 }
+// Tests on a double's bit pattern, on the integer pipe (FP64 compares take
+// the FP64 pipe, the gradient pass's bottleneck): x != 0 (NaN counts as
+// nonzero, as the FP64 test does), equality of two values that are never NaN
+// (+0 and -0 differ: a stale mark at worst), and lo < x < hi for lo, hi
+// positive and finite (positive doubles order as their bit patterns; negative
+// values and NaN fall outside).
+__device__ __forceinline__ bool nonzero_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+}
+__device__ __forceinline__ bool same_bits(double x, double y)
+{
+    return __double_as_longlong(x) == __double_as_longlong(y);
+}
+__device__ __forceinline__ bool inside_bits(double x, double lo, double hi)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long l = (unsigned long long)__double_as_longlong(lo);
+    const unsigned long long h = (unsigned long long)__double_as_longlong(hi);
+    return u - (l + 1ull) < h - (l + 1ull);
+}
+
 // 1 / d for d > 0 (normal, finite) by Newton-Raphson on f(r) = 1/r - d from the
 // hardware approximation (rcp.approx.ftz.f64, about 2^-22 relative): each
 // step r <- r + r (1 - d r) squares the relative error, so two give full FP64
@@ -527,8 +550,8 @@ __device__ __forceinline__ double2 trial_factors(double p, double r1_if_uncertai
 // inner-trial weight (times d ln P0 / d theta it is the Ea and nu score), and
 // Ks, the kappa score with d ln p / d kappa = (s - B/(1+B)) d ln B / d kappa
 // (s = 1 right, 0 left); Es, the innovation of the rail's current (left
-// trials' a - p minus right trials' a - p), is summed over the rail's lanes.
-// The per-zone probabilities (Eqs. 3-6, FP64) are cached until the rail's
+// trials' a - p minus right trials' a - p), is summed over the rail's lanes
+// (and left at zero when the current carries no weight).  The per-zone probabilities (Eqs. 3-6, FP64) are cached until the rail's
 // zone counts or V change.  With the exp tables,
 //   B_z = exp(gXV V) exp(gXV ka D'_z) exp(cm m_z),  m_z = L (Pb_z + Pb_z+1) - F,
 // three factors of which only the last changes with the zone counts, looked
@@ -544,26 +567,33 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
     const DevConst &K = *a.K;
     const double V = a.V[t];
     const bool act = seg < nact;
-    // A. one lane per rail: is the cache stale (V or a zone count changed)?
-    if (sl == 0 && act) {
+    const bool wantE = a.wJ != nullptr;   // the innovation pairs with the current's weight only
+    // A. is the rail's cache stale (V or a zone count changed)?  The rail's
+    //    lanes compare the prefix counts side by side; a ballot joins them.
+    bool changed;
+    {
         const int32_t *Pb = S.Pb() + seg * (Z + 1);
         int32_t *Pc = S.gPb() + seg * (Z + 2);
         double *rs = S.gS() + seg * 16;
-        bool changed = !(rs[6] == V);
-        for (int z = 0; z <= Z; ++z) changed |= Pb[z] != Pc[z];
-        Pc[Z + 1] = changed ? 1 : 0;
+        bool diff = false;
+        if (act) {
+            for (int z = sl; z <= Z; z += LPR) diff |= Pb[z] != Pc[z];
+            if (sl == 0) diff |= !same_bits(rs[6], V);
+        }
+        const uint32_t mine = LPR == 32 ? FULL : (((1u << (LPR & 31)) - 1u) << (seg * LPR));
+        changed = (__ballot_sync(FULL, diff) & mine) != 0u;
         if (changed) {
-            for (int z = 0; z <= Z; ++z) Pc[z] = Pb[z];
-            if (!(rs[6] == V)) rs[15] = exp(__dmul_rn(gXV, V));   // exp(gXV V)
-            rs[6] = V;
+            for (int z = sl; z <= Z; z += LPR) Pc[z] = Pb[z];
+            if (sl == 0) {
+                if (!same_bits(rs[6], V)) rs[15] = exp(__dmul_rn(gXV, V));   // exp(gXV V)
+                rs[6] = V;
+            }
         }
     }
     __syncwarp();
     double Wp = 0.0, Kp = 0.0, Ep = 0.0;
     if (act && sl < W2) {
         double *rs = S.gS() + seg * 16;
-        const bool changed = S.gPb()[seg * (Z + 2) + Z + 1] != 0;
-        const bool tabled = a.etL != nullptr && fabs(__dmul_rn(gXV, V)) < 600.0;
         for (int z = sl; z < Z; z += W2) {
             const int pi = seg * Z + z;
             if (changed) {
@@ -573,7 +603,7 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 const int m = L * (Pb[z] + Pb[z + 1]) - S.Fs()[seg];
                 const double dq = __fma_rn(0.5 * gInvL, (double)m, -S.gCz()[pi]);
                 double B;                                             // Eqs. 3-4
-                if (tabled) {
+                if (a.etL != nullptr && fabs(__dmul_rn(gXV, V)) < 600.0) {
                     const int u = m + a.etM;
                     B = __dmul_rn(__dmul_rn(rs[15], S.gEe()[pi]),
                                   __dmul_rn(__ldg(a.etH + (u >> 10)), __ldg(a.etL + (u & 1023))));
@@ -587,7 +617,7 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 const double y23 = __dmul_rn(y2, y3);
                 double inv, pL, pR;
                 const double xd = __dmul_rn(x1, y23);
-                if (xd > 1e-300 && xd < 1e300) {                       // both trials uncertain
+                if (inside_bits(xd, 1e-300, 1e300)) {                  // both trials uncertain
                     const double rp = recip_newton(xd);                // 1 / (x1 y2 y3)
                     const double x1rp = __dmul_rn(x1, rp), x1x1rp = __dmul_rn(x1, x1rp);
                     inv = __dmul_rn(y23, rp);
@@ -655,8 +685,9 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 Kp = __fma_rn(wR, dk.x, __fma_rn(wL, dk.y, Kp));
                 // left trials' a - p minus right trials' a - p: the integer part
                 // aL - aR and nR p_R - nL p_L
-                Ep = __dadd_rn(Ep, __fma_rn((double)nR, p.x,
-                                            __fma_rn(-(double)nL, p.y, (double)(aL - aR))));
+                if (wantE)
+                    Ep = __dadd_rn(Ep, __fma_rn((double)nR, p.x,
+                                                __fma_rn(-(double)nL, p.y, (double)(aL - aR))));
             }
             if (open && z == 0) {
                 const double dkR = S.gDK()[pi].x, dkL = S.gDK()[pi].y;
@@ -664,11 +695,11 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 if (S.ow()[idx] & 1u) {        // extraction through the left electrode
                     const int hit = (S.accL()[idx] & 1u) ? 1 : 0;
                     Kp = __fma_rn(et_weight(hit, rs[8], rs[12]), dkL, Kp);
-                    Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[8]));
+                    if (wantE) Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[8]));
                 } else {                       // injection into site 0
                     const int hit = (S.accR()[idx] & 1u) ? 1 : 0;
                     Kp = __fma_rn(et_weight(hit, rs[7], rs[11]), dkR, Kp);
-                    Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[7]));
+                    if (wantE) Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[7]));
                 }
             }
             if (open && z == Z - 1) {
@@ -678,17 +709,18 @@ __device__ __forceinline__ void grad_step_score(const SweepArgs &a, const WarpSm
                 if (S.ow()[idx] & bit) {       // extraction through the right electrode
                     const int hit = (S.accR()[idx] & bit) ? 1 : 0;
                     Kp = __fma_rn(et_weight(hit, rs[9], rs[13]), dkR, Kp);
-                    Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[9]));
+                    if (wantE) Ep = __dsub_rn(Ep, __dsub_rn((double)hit, rs[9]));
                 } else {                       // injection into site L-1
                     const int hit = (S.accL()[idx] & bit) ? 1 : 0;
                     Kp = __fma_rn(et_weight(hit, rs[10], rs[14]), dkL, Kp);
-                    Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[10]));
+                    if (wantE) Ep = __dadd_rn(Ep, __dsub_rn((double)hit, rs[10]));
                 }
             }
         }
     }
     // the rail's innovation, summed over its W2 zone lanes
-    for (int off = W2 >> 1; off >= 1; off >>= 1) Ep = __dadd_rn(Ep, __shfl_xor_sync(FULL, Ep, off, W2));
+    if (wantE)
+        for (int off = W2 >> 1; off >= 1; off >>= 1) Ep = __dadd_rn(Ep, __shfl_xor_sync(FULL, Ep, off, W2));
     Ws = Wp;
     Ks = Kp;
     Es = Ep;
@@ -1232,19 +1264,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 // by every lane to its share of the score
                 double d = 0.0;
                 if (sl == 0 && seg < nact) {
-                    if (a.fZa) {
+                    // zones outside [lo, hi) have zero weight and add nothing;
+                    // a step without weights has a zero share
+                    const int zr = a.fZa ? a.fZr[t] : 0;
+                    if (zr != 0) {
                         double fZ = -a.fZb[t];
-                        for (int z = 0; z < Z; ++z) {
+                        for (int z = zr & 255; z < (zr >> 8); ++z) {
                             const int nz = S.Pb()[seg * (Z + 1) + z + 1] - S.Pb()[seg * (Z + 1) + z];
                             fZ = __fma_rn(a.fZa[(int64_t)t * Z + z], (double)nz, fZ);
                         }
                         d = fZ;
                     }
                     if (a.wJ) d = __fma_rn(-a.wJ[t], Es, d);
-                    if (d != 0.0) S.gS()[seg * 16 + 4] = __dadd_rn(S.gS()[seg * 16 + 4], d);   // G_1
+                    if (nonzero_bits(d)) S.gS()[seg * 16 + 4] = __dadd_rn(S.gS()[seg * 16 + 4], d);   // G_1
                 }
                 d = __shfl_sync(FULL, d, 0, LPR);
-                if (d != 0.0) {
+                if (nonzero_bits(d)) {
                     aGW = __fma_rn(d, aW, aGW);
                     aGK = __fma_rn(d, aK, aGK);
                 }
@@ -1353,7 +1388,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const uint32_t *r
                 // every lane of the rail holds its J_t (Jrail)
                 if (a.wJ) {
                     const double2 ab = a.fJab[t];
-                    if (ab.x != 0.0 || ab.y != 0.0) {
+                    if (nonzero_bits(ab.x) || nonzero_bits(ab.y)) {
                         const double fJ = __fma_rn(ab.x, (double)Jrail, -ab.y);
                         aGW = __fma_rn(fJ, aW, aGW);
                         aGK = __fma_rn(fJ, aK, aGK);
@@ -1516,68 +1551,60 @@ __global__ void __launch_bounds__(1024) grad_reduce_kernel(const double *gs, int
             out[4 + i] = R > 1 ? sqrt(__dmul_rn(__ddiv_rn((double)R, (double)(R - 1)), sq[i])) : 0.0;
 }
 
-// Batch of devices in one persistent launch: CTAs take (device, rail tile)
-// work items from a shared counter and run the same tile body with that
-// device's arguments copied to shared memory.  The step index lives in device
-// memory so that a launch and its advance can be replayed as a CUDA graph.
-template <bool ACC>
-__global__ void __launch_bounds__(256, 3) sweep_batch_kernel(const BatchArgs b)
+// Batch of devices: one persistent launch per kernel shape (lanes per rail,
+// words per lane), so that each shape gets the registers of its own tile
+// body.  The launch's CTAs take (device, rail tile) items of that shape from
+// the shape's own counter and run the tile body with the device's arguments
+// copied to shared memory.  The step index lives in device memory so that the
+// launches and their advance can be replayed as a CUDA graph.
+template <bool ACC, int LPR, int WPL>
+__global__ void __launch_bounds__(256, ACC ? 4 : 5) sweep_batch_kernel(const BatchArgs b)
 {
+    constexpr int kind = shape_kind(LPR, WPL);
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SweepArgs ia;
     __shared__ int s_item;
     const int64_t t0 = *b.t0;
+    const int first = b.cls_off[kind], end = b.cls_off[kind + 1];
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.work, 1u);
+        if (threadIdx.x == 0) s_item = first + (int)atomicAdd(b.work + kind, 1u);
         __syncthreads();
         const int item = s_item;
-        if (item >= b.n_items) break;
+        if (item >= end) break;
         const BatchItem it = b.items[item];
         const uint32_t *src = (const uint32_t *)&b.inst[it.inst];
         for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs) / 4); i += blockDim.x)
             ((uint32_t *)&ia)[i] = src[i];
         __syncthreads();
-        switch (it.kind) {
-        case 0: sweep_tile<1, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 1: sweep_tile<2, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 2: sweep_tile<4, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 3: sweep_tile<8, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 4: sweep_tile<16, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        case 5: sweep_tile<32, 1, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        default: sweep_tile<32, 2, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem); break;
-        }
+        sweep_tile<LPR, WPL, ACC>(ia, b.rk0, b.rk1, t0, b.n_steps, b.flush, it.tile_rail0, smem);
         __syncthreads();
     }
 }
 
-// Gradient passes of a batch of devices in one persistent launch: CTAs take
-// (device, rail tile) items and replay that device's steps 0 .. n_steps-1
-// with its gradient-pass arguments (the same tile body as sweep_grad_kernel).
-__global__ void __launch_bounds__(256, 2) sweep_batch_grad_kernel(const BatchArgs b)
+// Gradient passes of a batch of devices, one persistent launch per kernel
+// shape: CTAs take (device, rail tile) items of that shape and replay that
+// device's steps 0 .. n_steps-1 with its gradient-pass arguments (the same
+// tile body as sweep_grad_kernel, at its 3 CTAs per SM).
+template <int LPR, int WPL>
+__global__ void __launch_bounds__(256, 3) sweep_batch_grad_kernel(const BatchArgs b)
 {
+    constexpr int kind = shape_kind(LPR, WPL);
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ SweepArgs ia;
     __shared__ int s_item;
+    const int first = b.cls_off[kind], end = b.cls_off[kind + 1];
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.work, 1u);
+        if (threadIdx.x == 0) s_item = first + (int)atomicAdd(b.work + kind, 1u);
         __syncthreads();
         const int item = s_item;
-        if (item >= b.n_items) break;
+        if (item >= end) break;
         const BatchItem it = b.items[item];
         const uint32_t *src = (const uint32_t *)&b.inst[it.inst];
         for (int i = threadIdx.x; i < (int)(sizeof(SweepArgs) / 4); i += blockDim.x)
             ((uint32_t *)&ia)[i] = src[i];
         __syncthreads();
         const int n = ia.n_steps;
-        switch (it.kind) {
-        case 0: sweep_tile<1, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        case 1: sweep_tile<2, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        case 2: sweep_tile<4, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        case 3: sweep_tile<8, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        case 4: sweep_tile<16, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        case 5: sweep_tile<32, 1, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        default: sweep_tile<32, 2, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem); break;
-        }
+        sweep_tile<LPR, WPL, true, true>(ia, b.rk0, b.rk1, 0, n, n, it.tile_rail0, smem);
         __syncthreads();
     }
 }
@@ -1633,12 +1660,12 @@ __global__ void __launch_bounds__(1024) batch_zone_scan_kernel(const BatchArgs b
     scan_zone_trace(ia.Zc, *b.t0, b.n_steps, ia.Z, blockIdx.x);
 }
 
-// Advance the batch's step counter and re-arm its work counter.
+// Advance the batch's step counter and re-arm the shapes' work counters.
 __global__ void batch_advance_kernel(int64_t *t0, unsigned *work, int n_steps)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        *t0 += n_steps;
-        *work = 0u;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *t0 += n_steps;
+        if (threadIdx.x < kShapeKinds) work[threadIdx.x] = 0u;
     }
 }
 
@@ -1737,17 +1764,52 @@ cudaError_t grad_launch(const SweepArgs &a, const SweepLaunch &l, cudaStream_t s
     }
 }
 
-cudaError_t batch_grad_launch(const BatchArgs &b, int grid, int warps, size_t smem, cudaStream_t s)
+// Calls f(lpr, wpl) with the lanes per rail and words per lane of shape kind
+// k as integral constants (the tile body's template arguments).
+template <class F>
+cudaError_t with_shape(int k, F &&f)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_batch_grad_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    using std::integral_constant;
+    switch (k) {
+    case 0: return f(integral_constant<int, 1>(), integral_constant<int, 1>());
+    case 1: return f(integral_constant<int, 2>(), integral_constant<int, 1>());
+    case 2: return f(integral_constant<int, 4>(), integral_constant<int, 1>());
+    case 3: return f(integral_constant<int, 8>(), integral_constant<int, 1>());
+    case 4: return f(integral_constant<int, 16>(), integral_constant<int, 1>());
+    case 5: return f(integral_constant<int, 32>(), integral_constant<int, 1>());
+    default: return f(integral_constant<int, 32>(), integral_constant<int, 2>());
     }
-    sweep_batch_grad_kernel<<<grid, warps * 32, smem, s>>>(b);
-    return cudaGetLastError();
+}
+
+cudaError_t batch_grad_launch(const BatchArgs &b, const BatchPlan &plan, int warps, cudaStream_t s)
+{
+    for (int k = 0; k < kShapeKinds; ++k) {
+        if (plan.grid[k] <= 0) continue;
+        const cudaError_t e = with_shape(k, [&](auto lpr, auto wpl) {
+            constexpr int P = decltype(lpr)::value, Q = decltype(wpl)::value;
+            sweep_batch_grad_kernel<P, Q><<<plan.grid[k], warps * 32, plan.smem[k], s>>>(b);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int batch_ctas_per_sm(int kind, int mode, int warps, size_t smem)
+{
+    int n = 0;
+    const cudaError_t e = with_shape(kind, [&](auto lpr, auto wpl) {
+        constexpr int P = decltype(lpr)::value, Q = decltype(wpl)::value;
+        if (mode == 2)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_batch_grad_kernel<P, Q>,
+                                                                 warps * 32, smem);
+        if (mode == 1)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_batch_kernel<true, P, Q>,
+                                                                 warps * 32, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_batch_kernel<false, P, Q>,
+                                                             warps * 32, smem);
+    });
+    return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 cudaError_t philox_probe(int grid, int iters, uint32_t *sink, cudaStream_t s)
@@ -1791,33 +1853,39 @@ cudaError_t sweep_set_smem_limits()
 
 int sweep_kind(int lpr, int wpl)
 {
-    if (wpl == 2) return 6;
-    switch (lpr) {
-    case 1: return 0;
-    case 2: return 1;
-    case 4: return 2;
-    case 8: return 3;
-    case 16: return 4;
-    default: return 5;
-    }
+    return shape_kind(lpr, wpl);
 }
 
 cudaError_t batch_set_smem_limit()
 {
-    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_batch_kernel<true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    for (int k = 0; k < kShapeKinds; ++k) {
+        const cudaError_t e = with_shape(k, [](auto lpr, auto wpl) {
+            constexpr int P = decltype(lpr)::value, Q = decltype(wpl)::value;
+            const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+            cudaError_t r = cudaFuncSetAttribute(sweep_batch_kernel<false, P, Q>, attr, 200 * 1024);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(sweep_batch_kernel<true, P, Q>, attr, 200 * 1024);
+            if (r == cudaSuccess) r = cudaFuncSetAttribute(sweep_batch_grad_kernel<P, Q>, attr, 200 * 1024);
+            return r;
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-cudaError_t batch_launch(const BatchArgs &b, int grid, int warps, size_t smem, bool acc,
+cudaError_t batch_launch(const BatchArgs &b, const BatchPlan &plan, int warps, bool acc,
                          cudaStream_t s)
 {
-    if (acc) sweep_batch_kernel<true><<<grid, warps * 32, smem, s>>>(b);
-    else sweep_batch_kernel<false><<<grid, warps * 32, smem, s>>>(b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    for (int k = 0; k < kShapeKinds; ++k) {
+        if (plan.grid[k] <= 0) continue;
+        e = with_shape(k, [&](auto lpr, auto wpl) {
+            constexpr int P = decltype(lpr)::value, Q = decltype(wpl)::value;
+            if (acc) sweep_batch_kernel<true, P, Q><<<plan.grid[k], warps * 32, plan.smem[k], s>>>(b);
+            else sweep_batch_kernel<false, P, Q><<<plan.grid[k], warps * 32, plan.smem[k], s>>>(b);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
     batch_zone_scan_kernel<<<dim3(b.max_z, b.n_inst), 1024, 0, s>>>(b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -26,7 +26,7 @@ def _batch_case(n, n_steps, seed=0):
     rng = np.random.default_rng(seed)
     devs, Vs, occs = [], [], []
     for i in range(n):
-        L = int(rng.choice([2, 31, 64, 100, 257, 700, 1024, 1500, 2048]))
+        L = int(rng.choice([2, 31, 64, 100, 200, 257, 700, 1024, 1500, 2048]))
         R = int(rng.integers(1, 90))
         Z = int(min(L, rng.choice([1, 4, 10])))
         el = int(rng.integers(0, 2))

@@ -64,6 +64,35 @@ def test_batched_gradient_passes_equal_per_device_passes(kmc):
     b.close()
 
 
+def test_batched_gradient_passes_of_every_kernel_shape(kmc):
+    """One device of every tile shape (lanes per rail 1 ... 32, and 32 lanes of
+    two words): the batched gradient pass runs one launch per shape and
+    returns, bit for bit, each device's own pass, with dense weights on some
+    devices and the fit's sparse first-zone weights on others."""
+    devs, V, fills, samples = W.fit_batch(7, seed=6, n_pulses=2, forget_steps=1000)
+    Ls = [20, 40, 100, 200, 400, 900, 1500]
+    devs = [dataclasses.replace(d, R=max(8, d.R // 64), L=L, Z=min(10, L)) for d, L in zip(devs, Ls)]
+    n = len(V)
+    b = kmc.Batch(devs, [V] * len(devs), [1] * len(devs), fills=fills)
+    b.step_n(n)
+    rng = np.random.default_rng(2)
+    wJs, wZs = [], []
+    for i, d in enumerate(devs):
+        if i % 2:
+            wZ = np.zeros((n, d.Z))
+            wZ[samples, 0] = rng.normal(size=len(samples))
+            wJs.append(None)
+            wZs.append(wZ)
+        else:
+            wJs.append(rng.normal(size=n))
+            wZs.append(rng.normal(size=(n, d.Z)))
+    g, se = b.grad_all(wJs, wZs)
+    for i in range(len(devs)):
+        gi, si = b.grad(i, wJs[i], wZs[i])
+        assert np.array_equal(g[i], gi, equal_nan=True) and np.array_equal(se[i], si, equal_nan=True), i
+    b.close()
+
+
 def _fit_case():
     """4 devices of 8,192 rails x 160 sites, 4 pulses + 4,000 steps; targets are
     the oracle's curves at the hidden (0.42 eV, 0.9) from 32 rails per device."""

@@ -85,6 +85,36 @@ def test_grad_observables_separately_and_deterministic(kmc):
     sim.close()
 
 
+@pytest.mark.parametrize("with_J", [False, True])
+def test_grad_sparse_zone_weights_match_oracle(kmc, with_J):
+    """Zone weights set at a few steps and zones only, as the fit's samples of
+    the first-zone count: the replay skips the zones outside each step's range
+    of nonzero weights and the steps without any, and still equals the
+    oracle's estimator (which sums every zone of every step)."""
+    Z = 10
+    dev = _dev(R=40, L=200, Z=Z, electrodes=1, k_e=1e6, rho_e=0.3, alpha=0.4)
+    V = _pulse(80, 170, 1.2)
+    n = len(V)
+    rng = np.random.default_rng(77)
+    wZ = np.zeros((n, Z))
+    wZ[::25, 0] = rng.normal(size=len(range(0, n, 25)))     # first zone, every 25th step
+    wZ[101, 3] = 0.7                                         # a range with a zero inside
+    wZ[101, 6] = -0.4
+    wZ[157, Z - 1] = 1.3                                     # the last zone alone
+    wZ[203, 4] = -0.0                                        # a signed zero counts as no weight
+    wJ = rng.normal(size=n) if with_J else None
+    sim = kmc.Sim(dev, V, init_mode=1, fill=0.3)
+    sim.step_n(n)
+    g, se = sim.grad(wJ, wZ)
+    occ0 = oracle.init_occupancy(dev, 1, fill=0.3)
+    ref = oracle.lr_gradient(dev, V, occ0, n, wJ=wJ, wZ=wZ, fill=0.3)
+    scale = np.abs(ref["G"]).sum(axis=0)
+    assert np.all(scale > 0)
+    assert np.all(np.abs(g - ref["grad"]) <= 1e-11 * scale + 1e-10 * np.abs(ref["grad"]))
+    np.testing.assert_allclose(se, ref["stderr"], rtol=1e-8)
+    sim.close()
+
+
 def test_grad_leaves_forward_state_unchanged(kmc):
     """The backward pass replays on its own buffers: stepping on after a
     gradient call gives the oracle's trajectory."""
