@@ -126,6 +126,22 @@ def test_per_site_barriers_bit_exact(kmc, L, electrodes):
     _compare(kmc, dev, V, occ0, Ea=Ea)
 
 
+@pytest.mark.parametrize("Z,sigma", [(3, 0.05), (10, 0.02), (12, 0.05), (16, 0.03), (20, 0.05),
+                                     (10, 0.0)])
+@pytest.mark.parametrize("accept", [0, 1])
+def test_per_site_barriers_zones_and_accept_paths_bit_exact(kmc, Z, sigma, accept):
+    """Per-site barriers on 513-1,024-site rails (the shape whose list entries
+    carry their bound row), from 3 to 20 zones, with a spread of barriers or
+    all equal, on both accept paths: the oracle's trajectory."""
+    R, L = 20, 700
+    dev = _dev(R=R, L=L, Z=Z, dt=5e-7 if accept else 1e-9, electrodes=1, k_e=1e6, rho_e=0.3,
+               seed=123 + Z)
+    occ0 = W.random_occupancy(R, L, 0.3, seed=Z)
+    Ea = W.normal_barriers(R, L, 0.40, sigma, seed=Z + 1) if sigma > 0 else np.full((R, L), 0.40)
+    V = W.triangle_protocol(2.5, 150, 2)
+    _compare(kmc, dev, V, occ0, Ea=Ea, accept=accept)
+
+
 def test_chunked_steps_and_launch_shapes_identical(kmc):
     dev = _dev(R=50, L=300, Z=7, electrodes=1, k_e=3e6, rho_e=0.4)
     occ0 = W.random_occupancy(50, 300, 0.35, seed=1)
