@@ -315,7 +315,7 @@ void kmc_batch_destroy(kmc_batch *b);
  * loading the library holds until the process exits; it limits n_rails to
  * KMC_NOALLOC_MAX_RAILS (larger sizes return KMC_E_ARG).  The first call on
  * a device looks up that array's device address and raises the kernels'
- * shared-memory limit, so make it before any stream capture.  All calls share
+ * shared-memory limit (host-side, once per device).  All calls share
  * the array: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The entry point zeroes
  * what has to start at zero (its counters, J_dev, zone_counts_dev) on
