@@ -241,12 +241,16 @@ const char *kmc_last_error(void);
  * device alone.  All devices share one seed (the Philox key) and are told
  * apart by their instance words (counter word 3); give them distinct ones.
  * V_per_step[i] is device i's host voltage table of n_steps_total entries;
- * init_occ_or_null may be NULL or hold NULL entries (for init_mode != 2).
- * Per-site barrier tables are not available in batches.  Errors as kmc_create. */
+ * init_occ_or_null may be NULL or hold NULL entries (for init_mode != 2);
+ * Ea_site_or_null may be NULL or hold NULL entries, and a non-NULL entry i is
+ * device i's per-site barrier table as kmc_create's Ea_site_or_null (host,
+ * FP64 [n_rails][n_sites], copied).  Devices with per-site barriers advance
+ * exactly as with kmc_create; their gradient passes are not available
+ * (kmc_grad's scalar-barrier rule).  Errors as kmc_create. */
 typedef struct kmc_batch kmc_batch;
 int kmc_batch_create(const kmc_params *params, int32_t n_inst, const double *const *V_per_step,
                      int64_t n_steps_total, const uint8_t *const *init_occ_or_null,
-                     void *cuda_stream, kmc_batch **out);
+                     const double *const *Ea_site_or_null, void *cuda_stream, kmc_batch **out);
 /* Advance every device by n_steps (asynchronous on the batch's stream). */
 int kmc_batch_step_n(kmc_batch *b, int64_t n_steps);
 /* kmc_observables for device `inst` of the batch (synchronizes). */

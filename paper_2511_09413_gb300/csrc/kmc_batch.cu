@@ -244,7 +244,7 @@ extern "C" {
 
 int kmc_batch_create(const kmc_params *params, int32_t n_inst, const double *const *V_per_step,
                      int64_t n_steps_total, const uint8_t *const *init_occ_or_null,
-                     void *cuda_stream, kmc_batch **out)
+                     const double *const *Ea_site_or_null, void *cuda_stream, kmc_batch **out)
 {
     if (!out) return fail(KMC_E_ARG, "out is NULL");
     *out = nullptr;
@@ -261,7 +261,8 @@ int kmc_batch_create(const kmc_params *params, int32_t n_inst, const double *con
     for (int i = 0; i < n_inst && rc == KMC_OK; ++i) {
         kmc_handle *h = nullptr;
         rc = kmc_create(&params[i], V_per_step[i], n_steps_total,
-                        init_occ_or_null ? init_occ_or_null[i] : nullptr, nullptr, cuda_stream, &h);
+                        init_occ_or_null ? init_occ_or_null[i] : nullptr,
+                        Ea_site_or_null ? Ea_site_or_null[i] : nullptr, cuda_stream, &h);
         if (rc == KMC_OK) b->dev.push_back(h);
     }
     auto bail = [&](int code) {

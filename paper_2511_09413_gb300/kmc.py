@@ -112,7 +112,7 @@ def load(path: str = LIB_PATH):
     L.kmc_sweep_noalloc.argtypes = [P(kmc_params), vp, i64, vp, vp, i64, i64, vp, vp, vp]
     L.kmc_sweep_noalloc.restype = ctypes.c_int
     L.kmc_batch_create.argtypes = [P(kmc_params), ctypes.c_int32, P(P(ctypes.c_double)), i64,
-                                   P(P(ctypes.c_uint8)), vp, P(vp)]
+                                   P(P(ctypes.c_uint8)), P(P(ctypes.c_double)), vp, P(vp)]
     L.kmc_batch_step_n.argtypes = [vp, i64]
     L.kmc_batch_observables.argtypes = [vp, ctypes.c_int32, i64, i64, P(ctypes.c_int64),
                                         P(ctypes.c_int64), P(ctypes.c_uint8)]
@@ -383,7 +383,8 @@ class Sim:
 
 # ----------------------------------------------------------------- batches
 
-def kmc_batch_create(params_list, V_list, init_occ_list=None, stream: int = 0) -> int:
+def kmc_batch_create(params_list, V_list, init_occ_list=None, stream: int = 0,
+                     Ea_site_list=None) -> int:
     n = len(params_list)
     P = (kmc_params * n)(*params_list)
     Vs = [np.ascontiguousarray(v, dtype=np.float64) for v in V_list]
@@ -396,8 +397,17 @@ def kmc_batch_create(params_list, V_list, init_occ_list=None, stream: int = 0) -
     if init_occ_list is not None:
         occs = [None if o is None else np.ascontiguousarray(o, dtype=np.uint8) for o in init_occ_list]
         Op = (ctypes.POINTER(ctypes.c_uint8) * n)(*[_ptr(o, ctypes.c_uint8) for o in occs])
+    eas = None
+    Ep = None
+    if Ea_site_list is not None:
+        eas = [None if e is None else np.ascontiguousarray(e, dtype=np.float64) for e in Ea_site_list]
+        for p, e in zip(params_list, eas):
+            if e is not None and e.size != p.n_rails * p.n_sites:
+                raise ValueError("Ea_site must have n_rails * n_sites entries")
+        Ep = (ctypes.POINTER(ctypes.c_double) * n)(*[_ptr(e, ctypes.c_double) for e in eas])
     h = ctypes.c_void_p()
-    _check(load().kmc_batch_create(P, n, Vp, n_total, Op, ctypes.c_void_p(stream), ctypes.byref(h)))
+    _check(load().kmc_batch_create(P, n, Vp, n_total, Op, Ep, ctypes.c_void_p(stream),
+                                   ctypes.byref(h)))
     return h.value
 
 
@@ -505,7 +515,7 @@ class Batch:
     """Many devices advanced together by one persistent launch per chunk."""
 
     def __init__(self, devs, Vs, init_modes, n_ions=None, fills=None, occ0s=None,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, Ea_sites=None):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -515,7 +525,7 @@ class Batch:
         self.params = [params_from_device(d, m, ni, f)
                        for d, m, ni, f in zip(devs, init_modes, n_ions, fills)]
         self.shapes = [(p.n_rails, p.n_sites, p.n_zones) for p in self.params]
-        self.h = kmc_batch_create(self.params, Vs, occ0s, stream)
+        self.h = kmc_batch_create(self.params, Vs, occ0s, stream, Ea_sites)
 
     @property
     def t(self) -> int:

@@ -43,9 +43,9 @@ def _batch_case(n, n_steps, seed=0):
     return devs, Vs, occs
 
 
-def _check_against_oracle(b, devs, Vs, occs, n_steps):
+def _check_against_oracle(b, devs, Vs, occs, n_steps, Eas=None):
     for i, (dev, V, occ0) in enumerate(zip(devs, Vs, occs)):
-        orc = oracle.OracleSim(dev, V, occ0)
+        orc = oracle.OracleSim(dev, V, occ0, None if Eas is None else Eas[i])
         Jo, Zo = orc.step_n(n_steps)
         Jg, Zg = b.traces(i)
         assert np.array_equal(Zg, Zo), i
@@ -122,4 +122,25 @@ def test_batch_with_brick_wall_devices(kmc):
     b.set_launch(8, 64)
     b.step_n(n_steps)
     _check_against_oracle(b, devs, Vs, occs, n_steps)
+    b.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_with_per_site_barriers_bit_exact(kmc, mode):
+    """Devices with per-site barrier tables (every other device, all tile
+    shapes) next to scalar-barrier devices in one batch, with graph replays
+    and either accept path: each device equals the oracle, and a gradient
+    pass on a per-site device is refused."""
+    n_steps = 300
+    devs, Vs, occs = _batch_case(12, n_steps, seed=8)
+    Eas = [W.normal_barriers(d["R"], d["L"], 0.40, 0.03, seed=100 + i) if i % 2 == 0 else None
+           for i, d in enumerate(devs)]
+    b = kmc.Batch(devs, Vs, [2] * len(devs), occ0s=occs, Ea_sites=Eas)
+    b.set_accept_path(mode)
+    b.set_launch(8, 128)
+    b.step_n(200)
+    b.step_n(100)
+    _check_against_oracle(b, devs, Vs, occs, n_steps, Eas)
+    with pytest.raises(kmc.KmcError):
+        b.grad(0, np.ones(n_steps), None)
     b.close()
