@@ -127,10 +127,10 @@ def test_batch_with_brick_wall_devices(kmc):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_batch_with_per_site_barriers_bit_exact(kmc, mode):
-    """Devices with per-site barrier tables (every other device, all tile
-    shapes) next to scalar-barrier devices in one batch, with graph replays
-    and either accept path: each device equals the oracle, and a gradient
-    pass on a per-site device is refused."""
+    """Devices with per-site barrier tables (every other device of a batch of
+    mixed tile shapes) next to scalar-barrier devices, with graph replays and
+    either accept path: each device equals the oracle, and a gradient pass on
+    a per-site device is refused."""
     n_steps = 300
     devs, Vs, occs = _batch_case(12, n_steps, seed=8)
     Eas = [W.normal_barriers(d["R"], d["L"], 0.40, 0.03, seed=100 + i) if i % 2 == 0 else None
