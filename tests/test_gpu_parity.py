@@ -323,12 +323,12 @@ def test_hysteresis_device_sampled_rails_full_size(kmc):
 
 def test_hysteresis_device_sampled_rails_whole_protocol(kmc):
     """The same device through its whole protocol (two +-2 V cycles, 2e5
-    steps, in the bench's 1,000-step launches): every 256th rail re-run on the
-    oracle matches, occupancy and per-rail current, at every 50,000-step
-    checkpoint, and the near-threshold decisions of those rails are logged
-    identically."""
+    steps, in the bench's 10,000-step kmc_step_n calls): every 256th rail
+    re-run on the oracle matches, occupancy and per-rail current, at every
+    50,000-step checkpoint, and the near-threshold decisions of those rails
+    are logged identically."""
     wl = W.hysteresis_65536x1024(steps_per_cycle=100000, cycles=2)
-    n_total, chunk, launch = len(wl.V), 50000, 1000
+    n_total, chunk, launch = len(wl.V), 50000, 10000
     assert n_total == 200000
     sim = kmc.Sim.from_workload(wl)
     ids = np.arange(0, wl.device.R, 256)
