@@ -8,7 +8,12 @@ magnitudes are unpinned; only the qualitative trends it states are tested:
 - I-V hysteresis (Fig. 2, Fig. S3): faster sweeps give lower peak current and
   narrower loops;
 - rails vs noise (S4.1): rails fluctuate independently, so the fluctuation of
-  the device signal falls as 1/sqrt(rails).
+  the device signal falls as 1/sqrt(rails);
+- potentiation and forgetting under a pulse train (Fig. 3, Fig. S4): the
+  conductance rises pulse by pulse and relaxes once the pulses stop; a longer
+  relaxation time tau is slower and more persistent, and its relaxation is
+  less noisy (Fig. S2).  tau is the hop time scale (Gamma_0 of Eq. 1 is
+  proportional to 1/tau), so a tau k times longer is nu / k here.
 """
 import numpy as np
 import pytest
@@ -103,3 +108,54 @@ def test_noise_falls_as_inverse_sqrt_rails():
     small, big = fluct(64), fluct(1024)
     for a, b in zip(small, big):
         assert 3.4 < a / b < 4.6     # sqrt(1024 / 64) = 4
+
+
+def _pulse_train(nu, R=128, n_pulses=8, forget=8000):
+    """Decile-1 conductance G(t) under n_pulses pulses of 0.8 V (0.25 ms on,
+    0.25 ms off at 2,000 steps per ms), then `forget` steps at 0 V."""
+    V = W.potentiation_protocol(n_pulses, forget, V_pulse=0.8, pulse_ms=0.25, gap_ms=0.25,
+                                steps_per_ms=2000)
+    G, _, _ = _decile1_trace(_dev(R, nu=nu, seed=7), V)
+    return G
+
+
+@pytest.fixture(scope="module")
+def pulse_trains():
+    # tau and 5 tau (Figs. 3 and S4 compare relaxation times 1 ms and 5 ms)
+    return {1: _pulse_train(1e12), 5: _pulse_train(2e11)}
+
+
+def _pulse_ends(G, n_pulses=8, period=1000, on=500):
+    return np.array([G[k * period + on - 20:k * period + on].mean() for k in range(n_pulses)])
+
+
+def test_pulse_train_potentiates_then_forgets(pulse_trains):
+    for tau, G in pulse_trains.items():
+        G0 = G[:20].mean()
+        ends = _pulse_ends(G)
+        assert G0 < ends[0] < ends[-1], (tau, G0, ends)
+        # forgetting: the conductance falls in every 2,000-step block after the train
+        blocks = G[8000:].reshape(4, 2000).mean(axis=1)
+        assert np.all(np.diff(blocks) < 0), (tau, blocks)
+        assert blocks[-1] > G0              # not yet back to the start
+    # the short tau saturates under the train: most of its gain comes from the
+    # first pulses, while the long tau keeps rising
+    e1, e5 = _pulse_ends(pulse_trains[1]), _pulse_ends(pulse_trains[5])
+    assert (e1[3] - e1[0]) > 3.0 * (e1[7] - e1[4])
+    assert np.all(np.diff(e5) > 0)
+
+
+def test_longer_tau_is_slower_and_more_persistent(pulse_trains):
+    gain, kept = {}, {}
+    for tau, G in pulse_trains.items():
+        G0 = G[:20].mean()
+        gain[tau] = _pulse_ends(G)[0] - G0
+        trained = G[7980:8000].mean() - G0
+        kept[tau] = (G[-200:].mean() - G0) / trained
+    assert gain[5] < 0.5 * gain[1]          # slower: less gained in the first pulse
+    assert kept[5] > 2.0 * kept[1]          # more persistent after the train
+
+
+def test_longer_tau_relaxes_with_less_noise(pulse_trains):
+    noise = {tau: np.diff(G[10000:]).std() for tau, G in pulse_trains.items()}
+    assert noise[5] < 0.75 * noise[1]
