@@ -13,7 +13,11 @@ magnitudes are unpinned; only the qualitative trends it states are tested:
   conductance rises pulse by pulse and relaxes once the pulses stop; a longer
   relaxation time tau is slower and more persistent, and its relaxation is
   less noisy (Fig. S2).  tau is the hop time scale (Gamma_0 of Eq. 1 is
-  proportional to 1/tau), so a tau k times longer is nu / k here.
+  proportional to 1/tau), so a tau k times longer is nu / k here;
+- the spike-timing (STDP) analogue of the abstract (reading R20, on a
+  shortened window): a post pulse (-1 V) before the pre pulse (+1 V)
+  potentiates, most when the pulses are close; the reverse order depresses,
+  the more the later the post pulse comes before the fixed readout.
 """
 import numpy as np
 import pytest
@@ -159,3 +163,17 @@ def test_longer_tau_is_slower_and_more_persistent(pulse_trains):
 def test_longer_tau_relaxes_with_less_noise(pulse_trains):
     noise = {tau: np.diff(G[10000:]).std() for tau, G in pulse_trains.items()}
     assert noise[5] < 0.75 * noise[1]
+
+
+def test_spike_pair_timing_sign_and_closeness():
+    """Delta G = G(t_pre + 10 ms) - G(t_pre^-) for pre/post delays of -8, -2,
+    +2 and +8 ms (1 ms pulses of +-1 V, 500 steps per ms)."""
+    spm, t_pre = 500, 10.0
+    dG = {}
+    for delay in (-8.0, -2.0, 2.0, 8.0):
+        V = W.spike_pair_protocol(delay, spm, t_pre_ms=t_pre, window_ms=t_pre + 10.0)
+        G, _, _ = _decile1_trace(_dev(128, dt=1e-3 / spm, seed=9), V)
+        i_pre = int(round(t_pre * spm))
+        dG[delay] = G[-1] - G[i_pre - 1]
+    assert dG[-2.0] > dG[-8.0] > 0.0, dG      # post before pre: potentiation, closer is stronger
+    assert dG[8.0] < dG[2.0] < 0.0, dG        # pre before post: depression, read at a fixed time
