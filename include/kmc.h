@@ -230,14 +230,15 @@ void kmc_destroy(kmc_handle *h);
 /* Message of the last failure on this thread ("" if none). */
 const char *kmc_last_error(void);
 
-/* ---- Batches: many devices advanced by one persistent launch.
+/* ---- Batches: many devices advanced by persistent launches.
  * A batch holds n_inst independent devices (each as kmc_create would make it,
  * with its own sizes, parameters, voltage table and occupancy) that advance
- * together.  Every launch covers all devices: CTAs take (device, rail tile)
- * work items, longest tiles first, from a shared counter, so devices of very
- * different sizes keep the GPU full.  A launch of steps_per_launch steps and
- * the advance of the batch's step counter are captured once as a CUDA graph
- * and replayed.  Results per device are identical to kmc_step_n on that
+ * together.  Every chunk of steps covers all devices with one persistent
+ * launch per tile shape (lanes per rail): its CTAs take (device, rail tile)
+ * work items of that shape, longest tiles first, from a shared counter, so
+ * devices of very different sizes keep the GPU full.  The launches of
+ * steps_per_launch steps, the zone-count scans and the advance of the
+ * batch's step counter are captured once as a CUDA graph and replayed.  Results per device are identical to kmc_step_n on that
  * device alone.  All devices share one seed (the Philox key) and are told
  * apart by their instance words (counter word 3); give them distinct ones.
  * V_per_step[i] is device i's host voltage table of n_steps_total entries;
@@ -278,8 +279,9 @@ int kmc_batch_accept_path(const kmc_batch *b);
  * occupancy).  Synchronizes the batch's stream. */
 int kmc_batch_grad(kmc_batch *b, int32_t inst, const double *dLoss_dJ, const double *dLoss_dZc,
                    double grad_out[4], double stderr_out[4]);
-/* The gradient passes of every device of the batch in one persistent launch
- * (the devices' rail tiles as work items, as the forward batch).  For device
+/* The gradient passes of every device of the batch, one persistent launch
+ * per tile shape (the devices' rail tiles as work items, as the forward
+ * batch).  For device
  * i, dLoss_dJ[i] and dLoss_dZc[i] are as kmc_grad's (either array of pointers,
  * or an entry, may be NULL); grad_out[i][4] and stderr_out[i][4] (may be NULL)
  * receive what kmc_grad would return for that device alone.  Synchronizes. */

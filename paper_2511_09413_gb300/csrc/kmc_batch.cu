@@ -1,6 +1,7 @@
-// kmc_batch.cu -- many devices advanced together: one persistent launch per
-// chunk of steps over all devices' rail tiles, replayed as a CUDA graph, with
-// the CTA size and the steps per launch chosen by a measuring autotuner.
+// kmc_batch.cu -- many devices advanced together: per chunk of steps, one
+// persistent launch per tile shape over all devices' rail tiles of that shape,
+// replayed as a CUDA graph, with the CTA size and the steps per launch chosen
+// by a measuring autotuner.
 //
 // Each device of a batch is an ordinary handle (kmc_create), so placement,
 // per-device constants and observables are exactly those of a single device;

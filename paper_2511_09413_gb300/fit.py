@@ -4,14 +4,15 @@ likelihood-ratio gradient.
 
 The curve of a device is its conductance G(t) = Zc_t[0] / N, the fraction of
 its N ions in the first zone (the first decile at Z = 10), sampled at given
-steps.  Each iteration advances all devices together in one batched
-persistent launch at the current (Ea, kappa), and the loss
+steps.  Each iteration advances all devices together in the batch's
+persistent launches (one per tile shape) at the current (Ea, kappa), and the
+loss
 
     loss = sum over devices d, samples k of (G_d(t_k) - G*_d(t_k))^2
 
 has the gradient sum_{d,k} 2 (G_d(t_k) - G*_d(t_k)) dE[G_d(t_k)]/d theta, whose
-expectations come from the devices' backward passes, run together in one
-batched launch (kmc_batch_grad_all), with the weights 2 (G - G*) / N on the
+expectations come from the devices' backward passes, run together in the
+batched gradient launches (kmc_batch_grad_all), with the weights 2 (G - G*) / N on the
 zone-0 counts.  The sampled G replaces its
 expectation in the factor 2 (G - G*), which is exact as the devices' rail
 counts grow (G's own variance is O(1 / ions)).

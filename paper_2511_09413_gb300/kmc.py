@@ -512,7 +512,8 @@ def kmc_batch_destroy(b: int):
 
 
 class Batch:
-    """Many devices advanced together by one persistent launch per chunk."""
+    """Many devices advanced together: per chunk of steps, one persistent launch
+    per tile shape."""
 
     def __init__(self, devs, Vs, init_modes, n_ions=None, fills=None, occ0s=None,
                  stream: Optional[int] = None, Ea_sites=None):
@@ -544,7 +545,8 @@ class Batch:
         kmc_batch_set_accept_path(self.h, mode)
 
     def grad_all(self, dLoss_dJ=None, dLoss_dZc=None):
-        """Gradients of every device in one persistent launch (kmc_batch_grad_all)."""
+        """Gradients of every device, one persistent launch per tile shape
+        (kmc_batch_grad_all)."""
         return kmc_batch_grad_all(self.h, self.shapes, self.t, dLoss_dJ, dLoss_dZc)
 
     def grad(self, inst: int, dLoss_dJ: Optional[np.ndarray] = None,
