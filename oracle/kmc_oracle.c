@@ -626,13 +626,17 @@ int orc_max_threads(void)
 int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64_t t0,
                int64_t n_steps, uint8_t *occ, const int32_t *N0, const double *wJ,
                const double *wZ, const int64_t *J_tot, const int64_t *Zc_tot, double *S_cum,
-               double *G, double *loglik, int64_t *J_out, int nthreads)
+               double *G, double *loglik, int64_t *J_out, int nthreads, int64_t cv_window,
+               double *cv_out)
 {
     const int R = P->R, L = P->L, Z = P->Z;
     if (L < 2 || Z < 1 || Z > ORC_MAX_ZONES || Z > L || R < 0) return -1;
     if (P->rule != 0) return -1;   /* the score hook follows the synchronous rule */
     if (t0 < 0 || t0 + n_steps > (int64_t)ORC_INIT_STEP) return -1;
     if ((wJ && !J_tot) || (wZ && !Zc_tot)) return -1;
+    if (cv_out && cv_window < 1) return -1;
+    const int64_t cvK = cv_out ? (n_steps + cv_window - 1) / cv_window : 0;
+    const int cvF = Z + 2;   /* features: 1, first moment / L, zone counts */
     const double P0scalar = orc_p0(P->nu, P->Ea, P->T, P->dt);
     const double E = -expm1(-(2.0 * P->k_e * P->dt));
     const double E_in = E * P->rho_e;
@@ -673,8 +677,26 @@ int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64
                 int64_t Jr = 0;
                 int64_t zc[ORC_MAX_ZONES];
                 for (int z = 0; z < Z; ++z) zc[z] = 0;
+                /* first moment of the step-start occupancy (control-variate feature) */
+                double m1 = 0.0;
+                if (cv_out) {
+                    const uint8_t *o = occ + (int64_t)r * L;
+                    for (int k = 0; k < L; ++k) m1 += (double)(k * o[k]);
+                    m1 /= (double)L;
+                }
                 rail_step(P, r, t, V[t], occ + (int64_t)r * L, N0[r], NULL, P0scalar, E_in, E_out,
                           mvR, mvL, next, &Jr, zc, NULL, 0, NULL, &acc);
+                if (cv_out) {
+                    /* score increments of this rail-step times the step-start features */
+                    const int64_t k = s / cv_window;
+                    for (int e = 0; e < 2; ++e) {
+                        const double psi = acc.s[e == 0 ? 0 : 2];
+                        double *cv = cv_out + (((int64_t)r * 2 + e) * cvK + k) * cvF;
+                        cv[0] += psi;
+                        cv[1] += psi * m1;
+                        for (int z = 0; z < Z; ++z) cv[2 + z] += psi * (double)acc.Nz[z];
+                    }
+                }
                 double *Sr = S_cum + 4 * (int64_t)r;
                 double *Gr = G + 4 * (int64_t)r;
                 /* zone counts at the start of step t pair with the score of steps < t */

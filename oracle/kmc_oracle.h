@@ -75,10 +75,22 @@ int orc_max_threads(void);
  * none when R == 1).  The sum of G over rails estimates dE[F]/dtheta without
  * bias (the eta term is a control variate: eta_rs has zero mean given the
  * state at the start of step s, and S_cum before step s is fixed by then).  loglik[r] (optional) accumulates the log-probability of the same
- * trial outcomes under parameters Pe.  J_out (optional) receives J_s. */
+ * trial outcomes under parameters Pe.  J_out (optional) receives J_s.
+ *
+ * Control-variate features (optional, cv_out non-NULL, cv_window >= 1): for
+ * rail r, score entry e (0: Ea, 1: kappa), window k = s / cv_window and
+ * feature f, cv_out[((r * 2 + e) * K + k) * F + f] (K = ceil(n_steps /
+ * cv_window), F = Z + 2) accumulates psi_e(s) phi_f(s): psi_e(s) is the
+ * rail-step's score increment of entry e, and phi(s) = (1, sum_k k occ[k] / L,
+ * N_0 .. N_{Z-1}) is taken from the step-start occupancy.  psi has zero mean
+ * given the step-start state, so every feature sum has zero mean, and any
+ * combination of them with coefficients fixed independently of the rail can
+ * be subtracted from the rail's term G without bias.  (The ν score is the Ea
+ * score times a constant, so the Ea features serve it too.) */
 int orc_run_lr(const orc_params *P, const orc_params *Pe, const double *V, int64_t t0,
                int64_t n_steps, uint8_t *occ, const int32_t *N0, const double *wJ,
                const double *wZ, const int64_t *J_tot, const int64_t *Zc_tot, double *S_cum,
-               double *G, double *loglik, int64_t *J_out, int nthreads);
+               double *G, double *loglik, int64_t *J_out, int nthreads, int64_t cv_window,
+               double *cv_out);
 
 #endif

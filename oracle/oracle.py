@@ -94,7 +94,8 @@ def lib():
         L.orc_run.restype = ctypes.c_int
         L.orc_max_threads.restype = ctypes.c_int
         L.orc_run_lr.argtypes = [P, P, f64p, ctypes.c_int64, ctypes.c_int64, u8p, i32p, f64p, f64p,
-                                 i64p, i64p, f64p, f64p, f64p, i64p, ctypes.c_int]
+                                 i64p, i64p, f64p, f64p, f64p, i64p, ctypes.c_int, ctypes.c_int64,
+                                 f64p]
         L.orc_run_lr.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -285,7 +286,8 @@ def init_score_rho(occ0: np.ndarray, fill: float) -> np.ndarray:
 
 def lr_gradient(dev, V: np.ndarray, occ0: np.ndarray, n_steps: int,
                 wJ: Optional[np.ndarray] = None, wZ: Optional[np.ndarray] = None,
-                fill: Optional[float] = None, dev_eval=None, nthreads: int = 0) -> dict:
+                fill: Optional[float] = None, dev_eval=None, nthreads: int = 0,
+                cv_windows: int = 0) -> dict:
     """Likelihood-ratio gradient of F = sum_s wJ[s] J_s + sum_{s,z} wZ[s,z] Zc_s[z]
     over steps 0 .. n_steps-1 of a device started from occ0 (scalar barrier).
 
@@ -295,7 +297,15 @@ def lr_gradient(dev, V: np.ndarray, occ0: np.ndarray, n_steps: int,
     (the Bernoulli filling that produced occ0) is given.  Returns a dict with
     grad, stderr (from the spread of the independent per-rail terms), G (per
     rail), S (cumulative score per rail), loglik (per rail, at dev_eval or dev)
-    and J (the replayed totals)."""
+    and J (the replayed totals).
+
+    With cv_windows = K > 0 it also returns the state-dependent control
+    variate's features (orc_run_lr's cv_out, [R][2][K][Z + 2]: the Ea and
+    kappa score increments of each of K equal time windows times the
+    step-start features 1, first moment / L and zone counts) and grad_cv,
+    stderr_cv, G_cv: the per-rail terms less their cross-fitted linear
+    prediction from those features (`cross_fit`), for Ea and nu from the Ea
+    features and for kappa from the kappa features; rho is left as is."""
     P = params(dev)
     Pe = params(dev_eval if dev_eval is not None else dev)
     occ = np.ascontiguousarray(occ0, dtype=np.uint8).reshape(P.R, P.L).copy()
@@ -311,19 +321,62 @@ def lr_gradient(dev, V: np.ndarray, occ0: np.ndarray, n_steps: int,
     J = np.zeros(n_steps, dtype=np.int64)
     wJc = None if wJ is None else np.ascontiguousarray(wJ, dtype=np.float64)
     wZc = None if wZ is None else np.ascontiguousarray(wZ, dtype=np.float64).reshape(n_steps, P.Z)
+    cv = None
+    window = 0
+    if cv_windows > 0:
+        window = -(-n_steps // cv_windows)
+        K = -(-n_steps // window)
+        cv = np.zeros((P.R, 2, K, P.Z + 2))
     rc = lib().orc_run_lr(ctypes.byref(P), ctypes.byref(Pe), _ptr(Vc, ctypes.c_double), 0,
                           n_steps, _ptr(occ, ctypes.c_uint8), _ptr(N0, ctypes.c_int32),
                           _ptr(wJc, ctypes.c_double), _ptr(wZc, ctypes.c_double),
                           _ptr(J_tot, ctypes.c_int64), _ptr(Zc_tot, ctypes.c_int64),
                           _ptr(S, ctypes.c_double), _ptr(G, ctypes.c_double),
-                          _ptr(ll, ctypes.c_double), _ptr(J, ctypes.c_int64), nthreads)
+                          _ptr(ll, ctypes.c_double), _ptr(J, ctypes.c_int64), nthreads,
+                          window, _ptr(cv, ctypes.c_double))
     if rc != 0:
         raise ValueError("orc_run_lr failed (%d)" % rc)
-    grad = G.sum(axis=0)
     R = P.R
-    stderr = np.sqrt(R / max(R - 1, 1) * ((G - G.mean(axis=0)) ** 2).sum(axis=0))
-    if fill is None:
-        grad[3] = np.nan
-        stderr[3] = np.nan
-    return {"grad": grad, "stderr": stderr, "G": G, "S": S, "loglik": ll, "J": J,
-            "J_tot": J_tot, "Zc_tot": Zc_tot}
+
+    def summary(T):
+        g = T.sum(axis=0)
+        se = np.sqrt(R / max(R - 1, 1) * ((T - T.mean(axis=0)) ** 2).sum(axis=0))
+        if fill is None:
+            g[3] = np.nan
+            se[3] = np.nan
+        return g, se
+
+    grad, stderr = summary(G)
+    out = {"grad": grad, "stderr": stderr, "G": G, "S": S, "loglik": ll, "J": J,
+           "J_tot": J_tot, "Zc_tot": Zc_tot}
+    if cv is not None:
+        Xe = cv[:, 0].reshape(R, -1)
+        Xk = cv[:, 1].reshape(R, -1)
+        G_cv = G.copy()
+        G_cv[:, 0] = cross_fit(G[:, 0], Xe)
+        G_cv[:, 1] = cross_fit(G[:, 1], Xe)
+        G_cv[:, 2] = cross_fit(G[:, 2], Xk)
+        out["cv"] = cv
+        out["G_cv"] = G_cv
+        out["grad_cv"], out["stderr_cv"] = summary(G_cv)
+    return out
+
+
+def cross_fit(y: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """y less its cross-fitted linear prediction from zero-mean features X
+    (one row per rail): the coefficients for the even rails are fitted (least
+    squares with an intercept) on the odd rails and vice versa, so each rail's
+    correction is independent of its own terms, and since E[X] = 0 the sum of
+    the corrected terms keeps the expectation of the sum of y."""
+    y = np.asarray(y, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    out = y.copy()
+    idx = np.arange(len(y))
+    for half in (0, 1):
+        fit, app = idx % 2 != half, idx % 2 == half
+        if fit.sum() <= X.shape[1] + 1 or not app.any():
+            continue
+        Xf = X[fit] - X[fit].mean(axis=0)
+        beta = np.linalg.lstsq(Xf, y[fit] - y[fit].mean(), rcond=None)[0]
+        out[app] = y[app] - X[app] @ beta
+    return out

@@ -117,11 +117,47 @@ def test_lr_gradient_matches_master_equation(electrodes, observable, nR, k_e, Vw
     d2 = dict(dev, R=R)
     occ0 = oracle.init_occupancy(d2, 1, fill=fill)
     r = oracle.lr_gradient(d2, V, occ0, n, wJ=wJ / R if observable == "current" else None,
-                           wZ=wZ / R if observable == "zone" else None, fill=fill)
+                           wZ=wZ / R if observable == "zone" else None, fill=fill, cv_windows=5)
     z = (r["grad"] - exact) / r["stderr"]
     assert np.all(np.abs(z) < 4.0), (r["grad"], r["stderr"], exact)
     # the comparison has power: every component is resolved to better than 35 %
     assert np.all(r["stderr"] < 0.35 * np.abs(exact)), (r["stderr"], exact)
+    # the cross-fitted state-dependent control variate keeps the estimator unbiased
+    z_cv = (r["grad_cv"] - exact) / r["stderr_cv"]
+    assert np.all(np.abs(z_cv) < 4.0), (r["grad_cv"], r["stderr_cv"], exact)
+
+
+def test_control_variate_features_have_zero_mean():
+    """Every feature sum of the control variate (a score increment times a
+    step-start feature) averages to zero over independent rails."""
+    dev = _dev(R=20000, L=16, Z=4, electrodes=1, k_e=2e5, rho_e=0.3, dt=1e-6)
+    occ0 = oracle.init_occupancy(dev, 1, fill=0.3)
+    V = W.triangle_protocol(0.4, 40, 2)
+    r = oracle.lr_gradient(dev, V, occ0, len(V), fill=0.3, cv_windows=4)
+    A = r["cv"].reshape(dev["R"], -1)
+    m = A.mean(axis=0)
+    se = A.std(axis=0, ddof=1) / np.sqrt(A.shape[0])
+    ok = se > 0
+    assert ok.sum() > 0.9 * A.shape[1]
+    assert np.all(np.abs(m[ok]) < 4.5 * se[ok]), np.abs(m[ok] / se[ok]).max()
+
+
+def test_control_variate_reduces_the_standard_error():
+    """Write pulse and relaxation on 4,096 rails x 64 sites, F = mean
+    relaxation current: the cross-fitted control variate over 10 time windows
+    cuts the standard error of the Ea, nu and kappa entries by more than a
+    third, and moves each estimate by less than the combined errors."""
+    R, nw, nr = 4096, 200, 800
+    dev = _dev(R=R, L=64, Z=8, dt=5e-7, alpha=0.2, seed=17)
+    occ0 = oracle.init_occupancy(dev, 1, fill=0.2)
+    V = np.concatenate([np.full(nw, 1.0), np.zeros(nr)])
+    w = np.zeros(nw + nr)
+    w[nw:] = 1.0 / (nr * R)
+    r = oracle.lr_gradient(dev, V, occ0, nw + nr, wJ=w, fill=0.2, cv_windows=10)
+    gain = r["stderr"][:3] / r["stderr_cv"][:3]
+    assert np.all(gain > 1.35), gain
+    assert np.all(np.abs(r["grad_cv"][:3] - r["grad"][:3]) < 3.0 * r["stderr"][:3])
+    assert r["grad_cv"][3] == r["grad"][3]          # no features for the filling
 
 
 def test_score_has_zero_mean():
